@@ -1,0 +1,155 @@
+/*
+ * ccpnk.h -- C ABI of the B300 closed-shell CCSD Newton-Krylov library (libccpnk.so).
+ *
+ * The problem (paper Sec. "Theory"): find amplitudes t = (t1, t2) with
+ *   r_mu(t) = <Phi_mu| e^{-T} H e^{T} |Phi_0> = 0  for all singles and doubles mu   (Eq. CC_ampl)
+ * and report E(t) = <Phi_0| e^{-T} H e^{T} |Phi_0> - E_ref                         (Eq. CC_energy).
+ * The paper works at the CCD level with 4-index integrals; this library solves
+ * closed-shell CCSD with density-fitted integrals (pq|rs) = sum_P B[P][p][q] B[P][r][s].
+ *
+ * Layouts (all row-major, FP64 on every precision path):
+ *   fock  n x n (n = o + v), occupied orbitals first; it is the Fock matrix of the
+ *         closed-shell reference, so the one-electron part is h = f - sum_k [2 (pq|kk) - (pk|kq)].
+ *   B     naux x n x n, B[P][p][q] == B[P][q][p] (checked to 1e-12 relative at cc_sys_create).
+ *   t1    o x v,          t1[i][a]       = t_i^a
+ *   t2    o x o x v x v,  t2[i][j][a][b] = t_ij^ab, with t_ij^ab = t_ji^ba.
+ *   r1/r2 same layouts as t1/t2: r1 is the alpha-alpha singles projection and r2
+ *         the alpha-beta doubles projection of e^{-T} H e^{T}|Phi_0>.
+ *   ||R|| is the Euclidean norm over the concatenation of r1 and r2.
+ *
+ * Memory: every amplitude/residual pointer may be host memory or device memory of the
+ * context's device; the library asks the CUDA runtime which it is. The caller owns
+ * every pointer it passes; the library never frees caller memory. cc_sys_create copies
+ * fock and B into device memory owned by the cc_sys handle.
+ *
+ * Streams: all device work of a context runs on the context's stream (the one passed to
+ * cc_ctx_create, or one the context creates). Calls return after that work is complete,
+ * except where stated. A context must not be used from two threads at once.
+ *
+ * Errors: every call returns CC_OK (0) or a negative status; cc_last_error() gives a
+ * one-line description of the last failure of that context.
+ */
+#ifndef CCPNK_H
+#define CCPNK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_OK 0
+#define CC_PENDING 1             /* cc_serve_poll: the request is still running */
+#define CC_ERR_INVALID (-1)      /* bad argument: NULL, o < 1, v < 1, naux < 1, B not symmetric */
+#define CC_ERR_OOM (-2)          /* device memory beyond the context's budget, or not admissible */
+#define CC_ERR_NOT_CONVERGED (-3) /* cc_solve hit its iteration cap; the report is filled */
+#define CC_ERR_DIVERGED (-4)     /* non-finite or exploding residual */
+#define CC_ERR_CUDA (-5)         /* a CUDA runtime error */
+#define CC_ERR_TIMEOUT (-6)      /* a bounded device-side wait gave up */
+
+typedef enum {
+  CC_FP64 = 0,          /* every contraction in FP64 (FMA pipe) */
+  CC_MIXED_TF32 = 1,    /* contractions of JVPs / inner solves on tcgen05 TF32, FP32 accumulate */
+  CC_MIXED_BF16X3 = 2   /* reserved: 3-pass BF16-split contractions (returns CC_ERR_INVALID today) */
+} cc_precision;
+
+typedef enum {
+  CC_FP_DIIS = 0,  /* fixed point with the diagonal-Fock denominator, level shift, DIIS (Eq. mo_fixed-point_update, App. D) */
+  CC_NK = 1,       /* Jacobian-free Newton-Krylov, no preconditioner (Table 1) */
+  CC_PNK = 2,      /* Newton-Krylov left-preconditioned by A_F (Eq. Preconditioner, Algorithm 1) */
+  CC_INK = 3       /* inexact Newton: step = A_F^{-1}(-r) (Eq. inexact_newton_update) */
+} cc_method;
+
+typedef struct cc_ctx cc_ctx;
+typedef struct cc_sys cc_sys;
+typedef struct cc_server cc_server;
+
+typedef struct {
+  cc_method method;
+  cc_precision prec;     /* precision of JVPs and of the inner A_F solves; the outer residual,
+                            energy, Newton update and Arnoldi orthogonalisation are always FP64 */
+  double tol;            /* stop when ||R|| < tol (default 1e-8) */
+  int max_outer;         /* Newton steps (NK/PNK/INK) or iterations (FP+DIIS); default 100 */
+  int m_max;             /* outer Arnoldi cap per Newton step (default 30) */
+  double gamma, alpha;   /* Eisenstat-Walker forcing (App. F.1): 0.9, 1.5 */
+  double eta_max;        /* forcing cap and eta_0 (default 0.9) */
+  double level_shift;    /* FP+DIIS denominator shift, App. D (default 0) */
+  int diis_size;         /* FP+DIIS subspace size (default 8; 0 disables DIIS) */
+  int jvp_fd;            /* 1: forward finite-difference JVP (Eq. jacobian_vector_product_via_finite_difference) */
+  double inner_rtol;     /* inner A_F GMRES relative tolerance (default 1e-12 FP64 / 1e-6 mixed) */
+  int inner_max;         /* inner GMRES cap (default 50) */
+  int af_direct;         /* 1: invert A_F in the Fock eigenbasis instead of by inner GMRES */
+  int verbose;           /* 1: one line per outer iteration on stderr */
+} cc_solve_opts;
+
+typedef struct {
+  double energy;         /* correlation energy at the returned amplitudes */
+  double res_norm;       /* FP64 ||R|| at the returned amplitudes */
+  int newton_iters;      /* Newton steps (or FP iterations) taken */
+  int residual_evals;    /* FP64 residual evaluations (the paper's cost metric) */
+  int jvps;              /* Jacobian-vector products */
+  int af_applies;        /* applications of A_F (inside inner solves) or of A_F^{-1} (direct) */
+  int krylov_iters;      /* total outer Arnoldi steps */
+  int status;            /* CC_OK, CC_ERR_NOT_CONVERGED or CC_ERR_DIVERGED */
+  double seconds;        /* wall time of the solve */
+} cc_report;
+
+/* Fills opts with the defaults listed above for the given method and precision. */
+void cc_solve_opts_default(cc_solve_opts* opts, cc_method method, cc_precision prec);
+
+/* Context on one device. mem_budget: bytes of device memory the context may hold
+ * (0 = no limit beyond the device). stream: a cudaStream_t, or NULL to create one. */
+int cc_ctx_create(cc_ctx** ctx, int device, size_t mem_budget, void* stream);
+void cc_ctx_destroy(cc_ctx* ctx);
+const char* cc_last_error(const cc_ctx* ctx);
+/* Device bytes currently held by the context's pools. */
+size_t cc_ctx_device_bytes(const cc_ctx* ctx);
+/* Number of kernel launches the context has issued since it was created. */
+uint64_t cc_ctx_launches(const cc_ctx* ctx);
+
+/* A problem resident on the device: copies fock (n x n) and B (naux x n x n), host or device. */
+int cc_sys_create(cc_ctx* ctx, int o, int v, int naux, const double* fock, const double* B, cc_sys** out);
+void cc_sys_destroy(cc_sys* sys);
+
+/* R(t) and E(t) (Eqs. CC_ampl, CC_energy). r1/r2 may be NULL to skip the copy-out;
+ * energy may be NULL. prec selects the contraction precision (CC_FP64 for the outer residual). */
+int cc_residual(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
+                double* r1, double* r2, double* energy, cc_precision prec);
+
+/* J(t) d, the exact directional derivative of R at t along d (App. B: every bilinear
+ * contraction becomes two). Mixed precisions run the contractions on tensor cores. */
+int cc_jvp(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
+           const double* d1, const double* d2, double* j1, double* j2, cc_precision prec);
+
+/* y = A_F x (inverse = 0) or y = A_F^{-1} x (inverse = 1), where
+ * (A_F x)_ij^ab = sum_c (f_ac x_ij^cb + f_bc x_ij^ac) - sum_k (f_ki x_kj^ab + f_kj x_ik^ab) and
+ * (A_F x)_i^a = sum_c f_ac x_i^c - sum_k f_ki x_k^a (Eq. Preconditioner, App. C; the factor 4
+ * printed there comes from an unnormalised projection and is not applied). The inverse is the
+ * inner GMRES of the solver (relative tolerance 1e-12 in FP64). */
+int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2,
+                double* y1, double* y2, int inverse, cc_precision prec);
+
+/* Solves R(t) = 0. t1/t2: on input the initial guess if use_guess != 0 (otherwise the
+ * generalised MP2 start t1 = 0, t2 = A_F^{-1}(-R2(0)) is used); on output the solution.
+ * Returns CC_OK, CC_ERR_NOT_CONVERGED or CC_ERR_DIVERGED with the report filled. */
+int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2,
+             int use_guess, cc_report* report);
+
+/* Continuous-batching server on one device: submitted solves are admitted while slots and
+ * device memory allow, run concurrently on the device, and complete independently. */
+int cc_server_create(cc_server** srv, int device, size_t mem_budget, int max_slots);
+void cc_server_destroy(cc_server* srv);
+/* Copies the problem (host pointers) before returning; ticket identifies the request. */
+int cc_serve_submit(cc_server* srv, int o, int v, int naux, const double* fock, const double* B,
+                    const cc_solve_opts* opts, uint64_t* ticket);
+/* CC_PENDING while the request runs; then its cc_solve status, with report filled and the
+ * solution copied to t1/t2 (host, may be NULL). A finished ticket is released by this call. */
+int cc_serve_poll(cc_server* srv, uint64_t ticket, cc_report* report, double* t1, double* t2);
+/* Timestamps of a finished request (seconds since server creation): submit, admit, finish. */
+int cc_serve_times(cc_server* srv, uint64_t ticket, double* t_submit, double* t_admit, double* t_finish);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCPNK_H */

@@ -1,0 +1,348 @@
+// The C ABI (include/ccpnk.h): contexts, resident problems, residual / JVP / A_F entry
+// points and the solver. Every entry point converts exceptions into a status code and a
+// per-context error message; no exception crosses the ABI.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+
+#include "solver.h"
+
+struct cc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::unique_ptr<ccpnk::Pool> pool;
+  uint64_t launches = 0;
+  int sm_count = 148;
+  std::string err;
+  ccpnk::Exec ex() {
+    ccpnk::Exec e;
+    e.stream = stream;
+    e.pool = pool.get();
+    e.launches = &launches;
+    e.sm_count = sm_count;
+    return e;
+  }
+};
+
+struct cc_sys {
+  cc_ctx* ctx = nullptr;
+  ccpnk::System s;
+  std::unique_ptr<ccpnk::Engine> eng;
+};
+
+namespace ccpnk {
+
+void fail(int status, const std::string& msg) { throw Error{status, msg}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) fail(CC_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    fail(CC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+Pool::~Pool() {
+  for (auto& b : blocks_) cudaFree(b.p);
+}
+
+void* Pool::get(size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  // best fit among free blocks no more than twice the request
+  int best = -1;
+  for (size_t i = 0; i < blocks_.size(); ++i) {
+    const Block& b = blocks_[i];
+    if (!b.used && b.bytes >= bytes && b.bytes <= 2 * bytes + 4096 &&
+        (best < 0 || b.bytes < blocks_[best].bytes))
+      best = (int)i;
+  }
+  if (best >= 0) {
+    blocks_[best].used = true;
+    return blocks_[best].p;
+  }
+  if (budget_ && held_ + bytes > budget_) release_free();
+  if (budget_ && held_ + bytes > budget_)
+    fail(CC_ERR_OOM, "device memory budget exceeded (" + std::to_string(held_ + bytes) + " > " +
+                         std::to_string(budget_) + " bytes)");
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release_free();
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(CC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+  }
+  blocks_.push_back({p, bytes, true});
+  held_ += bytes;
+  return p;
+}
+
+void Pool::put(void* p) {
+  for (auto& b : blocks_)
+    if (b.p == p) {
+      b.used = false;
+      return;
+    }
+}
+
+void Pool::release_free() {
+  std::vector<Block> keep;
+  for (auto& b : blocks_) {
+    if (b.used) keep.push_back(b);
+    else {
+      cudaFree(b.p);
+      held_ -= b.bytes;
+    }
+  }
+  blocks_.swap(keep);
+}
+
+}  // namespace ccpnk
+
+using namespace ccpnk;
+
+namespace {
+
+template <typename F>
+int guarded(cc_ctx* ctx, F&& f) {
+  try {
+    if (ctx) CC_CUDA(cudaSetDevice(ctx->device));
+    return f();
+  } catch (const Error& e) {
+    if (ctx) ctx->err = e.msg;
+    return e.status;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->err = e.what();
+    return CC_ERR_CUDA;
+  }
+}
+
+bool is_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void copy_in(cc_ctx* ctx, double* dst, const double* src, size_t n) {
+  if (!n) return;
+  CC_REQUIRE(src, CC_ERR_INVALID, "NULL input pointer");
+  CC_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), is_device(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          ctx->stream));
+}
+
+void copy_out(cc_ctx* ctx, double* dst, const double* src, size_t n) {
+  if (!n || !dst) return;
+  CC_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), is_device(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          ctx->stream));
+}
+
+Engine& engine(cc_sys* sys) {
+  if (!sys->eng) sys->eng.reset(new Engine(sys->ctx->ex(), sys->s));
+  return *sys->eng;
+}
+
+void check_prec(cc_precision p) {
+  CC_REQUIRE(p == CC_FP64 || p == CC_MIXED_TF32, CC_ERR_INVALID,
+             "precision not available (CC_FP64 and CC_MIXED_TF32 are)");
+}
+
+// [t1 | t2] with t2 symmetrised: T2 only depends on t_ij^ab + t_ji^ba
+void load_amplitudes(cc_ctx* ctx, const System& s, const double* t1, const double* t2, double* dst) {
+  const size_t ov = (size_t)s.o * s.v;
+  copy_in(ctx, dst, t1, ov);
+  DBuf<double> raw(ctx->pool.get(), s.namp() - ov);
+  copy_in(ctx, raw.p, t2, s.namp() - ov);
+  Exec ex = ctx->ex();
+  k_sym_add(ex, s.o, s.v, raw.p, dst + ov, 0.0);
+  k_scale(ex, s.namp() - ov, 0.5, dst + ov);
+}
+
+}  // namespace
+
+extern "C" {
+
+void cc_solve_opts_default(cc_solve_opts* o, cc_method method, cc_precision prec) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->method = method;
+  o->prec = prec;
+  o->tol = 1e-8;
+  o->max_outer = method == CC_FP_DIIS ? 500 : 100;
+  o->m_max = 30;
+  o->gamma = 0.9;
+  o->alpha = 1.5;
+  o->eta_max = 0.9;
+  o->level_shift = 0.0;
+  o->diis_size = 8;
+  o->jvp_fd = 0;
+  o->inner_rtol = prec == CC_FP64 ? 1e-12 : 1e-6;
+  o->inner_max = 50;
+  o->af_direct = 0;
+  o->verbose = 0;
+}
+
+int cc_ctx_create(cc_ctx** out, int device, size_t mem_budget, void* stream) {
+  if (!out) return CC_ERR_INVALID;
+  *out = nullptr;
+  std::unique_ptr<cc_ctx> c(new cc_ctx);
+  c->device = device;
+  int st = guarded(c.get(), [&]() {
+    int ndev = 0;
+    CC_CUDA(cudaGetDeviceCount(&ndev));
+    CC_REQUIRE(device >= 0 && device < ndev, CC_ERR_INVALID, "no such device");
+    CC_CUDA(cudaSetDevice(device));
+    CC_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    if (stream) {
+      c->stream = (cudaStream_t)stream;
+    } else {
+      CC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    c->pool.reset(new Pool(mem_budget));
+    return CC_OK;
+  });
+  if (st == CC_OK) *out = c.release();
+  return st;
+}
+
+void cc_ctx_destroy(cc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  ctx->pool.reset();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* cc_last_error(const cc_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+size_t cc_ctx_device_bytes(const cc_ctx* ctx) { return ctx && ctx->pool ? ctx->pool->held() : 0; }
+
+uint64_t cc_ctx_launches(const cc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int cc_sys_create(cc_ctx* ctx, int o, int v, int naux, const double* fock, const double* B, cc_sys** out) {
+  if (!ctx || !out) return CC_ERR_INVALID;
+  *out = nullptr;
+  return guarded(ctx, [&]() {
+    CC_REQUIRE(o >= 1 && v >= 1 && naux >= 1, CC_ERR_INVALID, "need o >= 1, v >= 1, naux >= 1");
+    CC_REQUIRE(fock && B, CC_ERR_INVALID, "NULL fock or B");
+    const int n = o + v;
+    Exec ex = ctx->ex();
+    DBuf<double> f(ex.pool, (size_t)n * n), b(ex.pool, (size_t)naux * n * n), chk(ex.pool, 4096);
+    copy_in(ctx, f.p, fock, (size_t)n * n);
+    copy_in(ctx, b.p, B, (size_t)naux * n * n);
+    k_asym(ex, naux, n, b.p, chk.p, chk.p + 2);
+    double h[2];
+    CC_CUDA(cudaMemcpyAsync(h, chk.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    CC_REQUIRE(std::isfinite(h[0]) && std::isfinite(h[1]), CC_ERR_INVALID, "B holds non-finite values");
+    CC_REQUIRE(h[0] <= 1e-12 * std::max(h[1], 1e-300), CC_ERR_INVALID, "B[P] is not symmetric in its orbital indices");
+    std::unique_ptr<cc_sys> s(new cc_sys);
+    s->ctx = ctx;
+    system_init(ex, s->s, o, v, naux, f.p, b.p);
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = s.release();
+    return CC_OK;
+  });
+}
+
+void cc_sys_destroy(cc_sys* sys) {
+  if (!sys) return;
+  cudaSetDevice(sys->ctx->device);
+  cudaStreamSynchronize(sys->ctx->stream);
+  delete sys;
+}
+
+int cc_residual(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2, double* r1, double* r2,
+                double* energy, cc_precision prec) {
+  if (!ctx || !sys) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    check_prec(prec);
+    const System& s = sys->s;
+    Engine& eng = engine(sys);
+    Exec ex = ctx->ex();
+    DBuf<double> t(ex.pool, s.namp()), r(ex.pool, s.namp()), e(ex.pool, 1);
+    load_amplitudes(ctx, s, t1, t2, t.p);
+    eng.value(t.p, r.p, e.p, prec);
+    const size_t ov = (size_t)s.o * s.v;
+    copy_out(ctx, r1, r.p, ov);
+    copy_out(ctx, r2, r.p + ov, s.namp() - ov);
+    double eh = 0.0;
+    CC_CUDA(cudaMemcpyAsync(&eh, e.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (energy) *energy = eh;
+    return CC_OK;
+  });
+}
+
+int cc_jvp(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2, const double* d1, const double* d2,
+           double* j1, double* j2, cc_precision prec) {
+  if (!ctx || !sys) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    check_prec(prec);
+    const System& s = sys->s;
+    Engine& eng = engine(sys);
+    Exec ex = ctx->ex();
+    DBuf<double> t(ex.pool, s.namp()), d(ex.pool, s.namp()), r(ex.pool, s.namp());
+    load_amplitudes(ctx, s, t1, t2, t.p);
+    load_amplitudes(ctx, s, d1, d2, d.p);
+    eng.value(t.p, r.p, nullptr, CC_FP64);
+    eng.tangent(d.p, r.p, prec);
+    const size_t ov = (size_t)s.o * s.v;
+    copy_out(ctx, j1, r.p, ov);
+    copy_out(ctx, j2, r.p + ov, s.namp() - ov);
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CC_OK;
+  });
+}
+
+int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2, double* y1, double* y2, int inverse,
+                cc_precision prec) {
+  if (!ctx || !sys) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    check_prec(prec);
+    System& s = sys->s;
+    Exec ex = ctx->ex();
+    DBuf<double> x(ex.pool, s.namp()), y(ex.pool, s.namp());
+    const size_t ov = (size_t)s.o * s.v;
+    copy_in(ctx, x.p, x1, ov);
+    copy_in(ctx, x.p + ov, x2, s.namp() - ov);
+    if (inverse == 0) apply_AF(ex, s, x.p, y.p, prec);
+    else if (inverse == 1) solve_AF(ex, s, x.p, y.p, prec, prec == CC_FP64 ? 1e-12 : 1e-6, 50, false, nullptr);
+    else solve_AF(ex, s, x.p, y.p, prec, 0.0, 0, true, nullptr);  // inverse == 2: eigenbasis inverse
+    copy_out(ctx, y1, y.p, ov);
+    copy_out(ctx, y2, y.p + ov, s.namp() - ov);
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CC_OK;
+  });
+}
+
+int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2, int use_guess,
+             cc_report* report) {
+  if (!ctx || !sys || !opts) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    check_prec(opts->prec);
+    CC_REQUIRE(opts->method >= CC_FP_DIIS && opts->method <= CC_INK, CC_ERR_INVALID, "unknown method");
+    System& s = sys->s;
+    Engine& eng = engine(sys);
+    Exec ex = ctx->ex();
+    DBuf<double> t(ex.pool, s.namp());
+    if (use_guess) load_amplitudes(ctx, s, t1, t2, t.p);
+    int st = solve(ex, s, eng, *opts, t.p, report, use_guess != 0);
+    const size_t ov = (size_t)s.o * s.v;
+    copy_out(ctx, t1, t.p, ov);
+    copy_out(ctx, t2, t.p + ov, s.namp() - ov);
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return st;
+  });
+}
+
+}  // extern "C"

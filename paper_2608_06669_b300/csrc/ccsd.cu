@@ -1,0 +1,318 @@
+// Closed-shell CCSD residual over density-fitted integrals, and its exact linearisation.
+//
+// The residual (Eq. CC_ampl projected on singles and doubles) is evaluated in the
+// T1-similarity-transformed form: the DF factor is dressed, Bt[P] = X B[P] Y with
+// X = 1 - t1, Y = 1 + t1 acting on the virtual-occupied block, which turns every singles
+// contribution into dressed integrals; the doubles residual is then the CCD residual of the
+// paper's App. A (ladders, rings, Fock-like intermediates, the Omega permutation) over the
+// dressed Hamiltonian, and the singles residual has four terms. Integrals are never formed
+// beyond o^2 v^2 blocks: the particle-particle ladder builds (ac|bd) for a block of a at a
+// time from Bt and contracts it at once.
+//
+// One program serves both the residual and the Jacobian-vector product: run in value mode it
+// computes R(t) and keeps every intermediate; run in tangent mode it computes the directional
+// derivative of each step, where a bilinear contraction C = A B becomes dA B + A dB
+// (App. B, Eq. AnalyticJVP) and the values of A and B are those kept from the residual at t.
+#include <algorithm>
+#include <cmath>
+
+#include "ccsd.h"
+
+namespace ccpnk {
+
+void k_transpose(const Exec& ex, int batch, int rows, int cols, const double* in, long long in_bs,
+                 long long in_ld, double* out, long long out_bs, long long out_ld);
+void k_copy3d(const Exec& ex, int batch, int rows, int cols, const double* src, long long sbs, long long sld,
+              double* dst, long long dbs, long long dld);
+
+void system_init(const Exec& ex, System& s, int o, int v, int P, const double* f, const double* B) {
+  s.o = o;
+  s.v = v;
+  s.n = o + v;
+  s.P = P;
+  const int n = s.n;
+  Pool* pl = ex.pool;
+  s.f.alloc(pl, (size_t)n * n);
+  s.h.alloc(pl, (size_t)n * n);
+  s.fdiag.alloc(pl, n);
+  s.Boo.alloc(pl, (size_t)P * o * o);
+  s.Bov.alloc(pl, (size_t)P * o * v);
+  s.Bvv.alloc(pl, (size_t)P * v * v);
+  s.Govov.alloc(pl, (size_t)o * v * o * v);
+  s.Lovov.alloc(pl, (size_t)o * v * o * v);
+  k_copy(ex, (size_t)n * n, f, s.f.p);
+  k_copy3d(ex, 1, n, 1, f, 0, n + 1, s.fdiag.p, 0, 1);  // the diagonal
+  k_copy3d(ex, P, o, o, B, (long long)n * n, n, s.Boo.p, (long long)o * o, o);
+  k_copy3d(ex, P, o, v, B + o, (long long)n * n, n, s.Bov.p, (long long)o * v, v);
+  k_copy3d(ex, P, v, v, B + (size_t)o * n + o, (long long)n * n, n, s.Bvv.p, (long long)v * v, v);
+  // h = f - sum_k [2 (pq|kk) - (pk|kq)]
+  DBuf<double> gam(pl, P);
+  k_trace_batched(ex, P, o, s.Boo.p, gam.p);
+  k_copy(ex, (size_t)n * n, f, s.h.p);
+  double* Bm = const_cast<double*>(B);
+  contract(ex, CC_FP64, -2.0, view(Bm, "Xpq", {P, n, n}), view(gam.p, "X", {P}), 1.0, view(s.h.p, "pq", {n, n}));
+  contract(ex, CC_FP64, 1.0, view_strided(Bm, "Xpk", {P, n, o}, {(long long)n * n, n, 1}),
+           view_strided(Bm, "Xkq", {P, o, n}, {(long long)n * n, n, 1}), 1.0, view(s.h.p, "pq", {n, n}));
+  // (kc|ld) and its exchange combination, constant for the problem
+  contract(ex, CC_FP64, 1.0, view(s.Bov.p, "Xkc", {P, o, v}), view(s.Bov.p, "Xld", {P, o, v}), 0.0,
+           view(s.Govov.p, "kcld", {o, v, o, v}));
+  k_make_L_ovov(ex, o, v, s.Govov.p, s.Lovov.p);
+}
+
+Engine::Engine(const Exec& ex, const System& s) : ex_(ex), s_(s) {
+  const int o = s.o, v = s.v, n = s.n, P = s.P;
+  const size_t oovv = (size_t)o * o * v * v;
+  alloc(t_, s.namp());
+  alloc(u_, oovv);
+  alloc(Btoo_, (size_t)P * o * o);
+  alloc(Btvv_, (size_t)P * v * v);
+  alloc(Btvo_, (size_t)P * v * o);
+  alloc(gam_, P);
+  alloc(hY_, (size_t)n * n);
+  alloc(Ft_, (size_t)n * n);
+  alloc(Z_, (size_t)P * o * v);
+  alloc(Wk_, (size_t)P * o * v);
+  alloc(Woo_, (size_t)o * o * o * o);
+  alloc(Cint_, oovv);
+  alloc(Dint_, oovv);
+  alloc(Gv_, (size_t)v * v);
+  alloc(Go_, (size_t)o * o);
+  alloc(X_, oovv);
+  alloc(Y2_, oovv);
+  // ladder workspace: blocks of a with an (a, b, c, d) slab of at most ~512 MB
+  const double cap = 512.0 * 1024 * 1024;
+  const double per_a = 8.0 * (double)v * v * v;
+  ladder_block_ = std::max(1, std::min(v, (int)(cap / std::max(per_a, 1.0))));
+  W_.alloc(ex.pool, (size_t)ladder_block_ * v * v * v);
+  scratch_.alloc(ex.pool, 64 * 1024);
+}
+
+void Engine::alloc(Pair& x, size_t n) {
+  x.val.alloc(ex_.pool, n);
+  x.tan.alloc(ex_.pool, n);
+}
+
+namespace {
+
+// A tensor of the program: its value view and, if it depends on the amplitudes, its tangent view.
+struct TP {
+  TView v, t;
+  bool dyn = false;
+};
+
+}  // namespace
+
+void Engine::ladder(const double* Xv, const double* Yv, const double* T, double* R, cc_precision prec) {
+  // R[i][j][a][b] += sum_{P,c,d} X[P][a][c] Y[P][b][d] T[i][j][c][d]
+  const int o = s_.o, v = s_.v, P = s_.P;
+  double* X = const_cast<double*>(Xv);
+  double* Y = const_cast<double*>(Yv);
+  double* Tm = const_cast<double*>(T);
+  for (int a0 = 0; a0 < v; a0 += ladder_block_) {
+    const int al = std::min(ladder_block_, v - a0);
+    TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {P, al, v}, {(long long)v * v, v, 1});
+    TView W = view(W_.p, "abcd", {al, v, v, v});
+    contract(ex_, prec, 1.0, Xa, view(Y, "Pbd", {P, v, v}), 0.0, W);
+    TView Rv = view_strided(R + (size_t)a0 * v, "ijab", {o, o, al, v}, {(long long)o * v * v, (long long)v * v, v, 1});
+    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 1.0, Rv);
+  }
+}
+
+void Engine::program(bool tan, cc_precision prec, double* rout) {
+  const int o = s_.o, v = s_.v, n = s_.n, P = s_.P;
+  const size_t ov = (size_t)o * v, oovv = (size_t)o * o * v * v;
+  const Exec& ex = ex_;
+
+  auto dyn = [&](Pair& x, size_t off, const char* lab, std::initializer_list<int> ext) {
+    TP r;
+    r.v = view(x.val.p + off, lab, ext);
+    r.t = view(x.tan.p + off, lab, ext);
+    r.dyn = true;
+    return r;
+  };
+  auto dyns = [&](Pair& x, size_t off, const char* lab, std::initializer_list<int> ext,
+                  std::initializer_list<long long> st) {
+    TP r;
+    r.v = view_strided(x.val.p + off, lab, ext, st);
+    r.t = view_strided(x.tan.p + off, lab, ext, st);
+    r.dyn = true;
+    return r;
+  };
+  auto cst = [&](const double* p, const char* lab, std::initializer_list<int> ext) {
+    TP r;
+    r.v = view(const_cast<double*>(p), lab, ext);
+    r.t = r.v;
+    return r;
+  };
+  auto csts = [&](const double* p, const char* lab, std::initializer_list<int> ext,
+                  std::initializer_list<long long> st) {
+    TP r;
+    r.v = view_strided(const_cast<double*>(p), lab, ext, st);
+    r.t = r.v;
+    return r;
+  };
+  // the output vector is the value in value mode and the tangent in tangent mode
+  auto out = [&](size_t off, const char* lab, std::initializer_list<int> ext) {
+    TP r;
+    r.v = view(rout + off, lab, ext);
+    r.t = r.v;
+    r.dyn = true;
+    return r;
+  };
+  // C = alpha A B + beta C, linearised in tangent mode
+  auto bil = [&](double alpha, const TP& A, const TP& B, double beta, const TP& C) {
+    if (!tan) {
+      contract(ex, prec, alpha, A.v, B.v, beta, C.v);
+      return;
+    }
+    double b = beta;
+    if (A.dyn) {
+      contract(ex, prec, alpha, A.t, B.v, b, C.t);
+      b = 1.0;
+    }
+    if (B.dyn) {
+      contract(ex, prec, alpha, A.v, B.t, b, C.t);
+      b = 1.0;
+    }
+  };
+  auto cur = [&](Pair& x) { return tan ? x.tan.p : x.val.p; };
+
+  TP T1 = dyn(t_, 0, "ia", {o, v});
+  auto t1l = [&](const char* l) { return dyn(t_, 0, l, {o, v}); };
+  auto t2l = [&](const char* l) { return dyn(t_, ov, l, {o, o, v, v}); };
+  auto ul = [&](const char* l) { return dyn(u_, 0, l, {o, o, v, v}); };
+  auto Boo = [&](const char* l) { return dyn(Btoo_, 0, l, {P, o, o}); };
+  auto Bvv = [&](const char* l) { return dyn(Btvv_, 0, l, {P, v, v}); };
+  auto Bvo = [&](const char* l) { return dyn(Btvo_, 0, l, {P, v, o}); };
+  auto Bov = [&](const char* l) { return cst(s_.Bov.p, l, {P, o, v}); };
+  auto Gl = [&](const char* l) { return cst(s_.Govov.p, l, {o, v, o, v}); };
+  (void)T1;
+
+  // amplitudes u = 2 t - t(i<->j)
+  k_make_u(ex, o, v, cur(t_) + ov, cur(u_));
+
+  // ---- a1: T1 dressing of the DF factor -------------------------------------------------
+  // Bt_oo = B_oo + B_ov t1^T
+  if (!tan) k_copy(ex, (size_t)P * o * o, s_.Boo.p, Btoo_.val.p);
+  bil(1.0, Bov("Pic"), t1l("jc"), tan ? 0.0 : 1.0, Boo("Pij"));
+  // Bt_vv = B_vv - t1^T B_ov
+  if (!tan) k_copy(ex, (size_t)P * v * v, s_.Bvv.p, Btvv_.val.p);
+  bil(-1.0, t1l("ka"), Bov("Pkb"), tan ? 0.0 : 1.0, Bvv("Pab"));
+  // Bt_vo = B_vo + B_vv t1^T - t1^T Bt_oo
+  if (!tan) k_transpose(ex, P, o, v, s_.Bov.p, (long long)o * v, v, Btvo_.val.p, (long long)v * o, o);
+  bil(1.0, cst(s_.Bvv.p, "Pac", {P, v, v}), t1l("ic"), tan ? 0.0 : 1.0, Bvo("Pai"));
+  bil(-1.0, t1l("ka"), Boo("Pki"), 1.0, Bvo("Pai"));
+  k_trace_batched(ex, P, o, cur(Btoo_), cur(gam_));
+
+  // ---- dressed Fock matrix Ft = X h Y + 2 sum_P Bt gamma - sum_Pk Bt_pk Bt_kq -----------
+  if (!tan) k_copy(ex, (size_t)n * n, s_.h.p, hY_.val.p);
+  else k_fill(ex, (size_t)n * n, 0.0, hY_.tan.p);
+  bil(1.0, csts(s_.h.p + o, "pc", {n, v}, {n, 1}), t1l("jc"), 1.0, dyns(hY_, 0, "pj", {n, o}, {n, 1}));
+  k_copy(ex, (size_t)n * n, cur(hY_), cur(Ft_));
+  bil(-1.0, t1l("ka"), dyns(hY_, 0, "kq", {o, n}, {n, 1}), 1.0, dyns(Ft_, (size_t)o * n, "aq", {v, n}, {n, 1}));
+  TP Foo = dyns(Ft_, 0, "ij", {o, o}, {n, 1});
+  TP Fov = dyns(Ft_, o, "kc", {o, v}, {n, 1});
+  TP Fvo = dyns(Ft_, (size_t)o * n, "ai", {v, o}, {n, 1});
+  TP Fvv = dyns(Ft_, (size_t)o * n + o, "ab", {v, v}, {n, 1});
+  TP gam = dyn(gam_, 0, "P", {P});
+  bil(2.0, Boo("Pij"), gam, 1.0, Foo);
+  bil(2.0, Bov("Pkc"), gam, 1.0, Fov);
+  bil(2.0, Bvo("Pai"), gam, 1.0, Fvo);
+  bil(2.0, Bvv("Pab"), gam, 1.0, Fvv);
+  bil(-1.0, Boo("Pik"), Boo("Pkj"), 1.0, Foo);
+  bil(-1.0, Boo("Pkl"), Bov("Plc"), 1.0, Fov);
+  bil(-1.0, Bvo("Pak"), Boo("Pki"), 1.0, Fvo);
+  bil(-1.0, Bvo("Pak"), Bov("Pkb"), 1.0, Fvv);
+
+  // ---- singles residual -----------------------------------------------------------------
+  TP R1 = out(0, "ia", {o, v});
+  k_transpose(ex, 1, v, o, cur(Ft_) + (size_t)o * n, 0, n, rout, 0, v);  // Ft_vo^T
+  bil(1.0, Bov("Pkc"), ul("kicd"), 0.0, dyn(Z_, 0, "Pid", {P, o, v}));
+  bil(1.0, dyn(Z_, 0, "Pid", {P, o, v}), Bvv("Pad"), 1.0, R1);
+  bil(1.0, Bov("Plc"), ul("klac"), 0.0, dyn(Wk_, 0, "Pka", {P, o, v}));
+  bil(-1.0, Boo("Pki"), dyn(Wk_, 0, "Pka", {P, o, v}), 1.0, R1);
+  bil(1.0, ul("ikac"), dyns(Ft_, o, "kc", {o, v}, {n, 1}), 1.0, R1);
+
+  // ---- doubles residual -----------------------------------------------------------------
+  TP R2 = out(ov, "ijab", {o, o, v, v});
+  double* r2 = rout + ov;
+  // (ai|bj)~
+  bil(1.0, Bvo("Pai"), Bvo("Pbj"), 0.0, R2);
+  // particle-particle ladder sum_cd (ac|bd)~ t_ij^cd
+  if (!tan) {
+    ladder(Btvv_.val.p, Btvv_.val.p, t_.val.p + ov, r2, prec);
+  } else {
+    ladder(Btvv_.val.p, Btvv_.val.p, t_.tan.p + ov, r2, prec);
+    k_fill(ex, oovv, 0.0, Y2_.val.p);
+    ladder(Btvv_.tan.p, Btvv_.val.p, t_.val.p + ov, Y2_.val.p, prec);
+    k_sym_add(ex, o, v, Y2_.val.p, r2, 1.0);  // the (a c)<->(b d) partner of the same term
+  }
+  // hole ladder with its quadratic part: W_klij = (ki|lj)~ + sum_cd (kc|ld) t_ij^cd
+  TP Woo = dyn(Woo_, 0, "klij", {o, o, o, o});
+  bil(1.0, Boo("Pki"), Boo("Plj"), 0.0, Woo);
+  bil(1.0, Gl("kcld"), t2l("ijcd"), 1.0, Woo);
+  bil(1.0, Woo, t2l("klab"), 1.0, R2);
+  // C_kiac = (ki|ac)~ - 1/2 sum_ld t_li^ad (kd|lc), stored [k][c][i][a]
+  auto Cl = [&](const char* l) { return dyn(Cint_, 0, l, {o, v, o, v}); };
+  bil(1.0, Boo("Pki"), Bvv("Pac"), 0.0, Cl("kcia"));
+  bil(-0.5, t2l("liad"), Gl("kdlc"), 1.0, Cl("kcia"));
+  TP X = dyn(X_, 0, "ijab", {o, o, v, v});
+  bil(-0.5, Cl("kcia"), t2l("kjbc"), 0.0, X);
+  bil(-1.0, Cl("kcja"), t2l("kibc"), 1.0, X);
+  // D_aikc = 2 (ai|kc)~ - (ac|ki)~ + 1/2 sum_ld u_il^ad L_ldkc, stored [k][c][i][a]
+  auto Dl = [&](const char* l) { return dyn(Dint_, 0, l, {o, v, o, v}); };
+  bil(2.0, Bvo("Pai"), Bov("Pkc"), 0.0, Dl("kcia"));
+  bil(-1.0, Bvv("Pac"), Boo("Pki"), 1.0, Dl("kcia"));
+  bil(0.5, ul("ilad"), cst(s_.Lovov.p, "ldkc", {o, v, o, v}), 1.0, Dl("kcia"));
+  bil(0.5, Dl("kcia"), ul("jkbc"), 1.0, X);
+  // Fock-like intermediates
+  k_copy3d(ex, 1, v, v, cur(Ft_) + (size_t)o * n + o, 0, n, cur(Gv_), 0, v);
+  bil(-1.0, ul("klbd"), Gl("ldkc"), 1.0, dyn(Gv_, 0, "bc", {v, v}));
+  k_copy3d(ex, 1, o, o, cur(Ft_), 0, n, cur(Go_), 0, o);
+  bil(1.0, ul("ljcd"), Gl("kdlc"), 1.0, dyn(Go_, 0, "kj", {o, o}));
+  bil(1.0, t2l("ijac"), dyn(Gv_, 0, "bc", {v, v}), 1.0, X);
+  bil(-1.0, t2l("ikab"), dyn(Go_, 0, "kj", {o, o}), 1.0, X);
+  // Omega permutation: R_ij^ab += X_ij^ab + X_ji^ba
+  k_sym_add(ex, o, v, cur(X_), r2, 1.0);
+  (void)Fvo;
+  (void)Fvv;
+}
+
+void Engine::value(const double* t, double* r, double* energy_dev, cc_precision prec) {
+  const int o = s_.o, v = s_.v, n = s_.n;
+  if (t != t_.val.p) k_copy(ex_, s_.namp(), t, t_.val.p);
+  program(false, prec, r);
+  if (energy_dev)
+    k_energy(ex_, o, v, s_.Govov.p, t_.val.p, t_.val.p + (size_t)o * v, s_.f.p + o, n, energy_dev, scratch_.p);
+}
+
+void Engine::tangent(const double* d, double* jd, cc_precision prec) {
+  if (d != t_.tan.p) k_copy(ex_, s_.namp(), d, t_.tan.p);
+  program(true, prec, jd);
+}
+
+// ---------------------------------------------------------------------------
+// A_F (Eq. Preconditioner, App. C): the occupied and virtual Fock blocks on every index
+// ---------------------------------------------------------------------------
+void apply_AF(const Exec& ex, const System& s, const double* xin, double* y, cc_precision prec) {
+  const int o = s.o, v = s.v, n = s.n;
+  const size_t ov = (size_t)o * v;
+  double* x = const_cast<double*>(xin);
+  TView foo = view_strided(s.f.p, "ki", {o, o}, {n, 1});
+  auto fvv = [&](const char* l) { return view_strided(s.f.p + (size_t)o * n + o, l, {v, v}, {n, 1}); };
+  auto fo = [&](const char* l) { return view_strided(s.f.p, l, {o, o}, {n, 1}); };
+  (void)foo;
+  // singles: y_i^a = sum_c f_ac x_i^c - sum_k f_ki x_k^a
+  contract(ex, prec, 1.0, view(x, "ic", {o, v}), fvv("ac"), 0.0, view(y, "ia", {o, v}));
+  contract(ex, prec, -1.0, fo("ki"), view(x, "ka", {o, v}), 1.0, view(y, "ia", {o, v}));
+  // doubles
+  double* x2 = x + ov;
+  double* y2 = y + ov;
+  TView Y = view(y2, "ijab", {o, o, v, v});
+  contract(ex, prec, 1.0, fvv("ac"), view(x2, "ijcb", {o, o, v, v}), 0.0, Y);
+  contract(ex, prec, 1.0, view(x2, "ijac", {o, o, v, v}), fvv("bc"), 1.0, Y);
+  contract(ex, prec, -1.0, fo("ki"), view(x2, "kjab", {o, o, v, v}), 1.0, Y);
+  contract(ex, prec, -1.0, view(x2, "ikab", {o, o, v, v}), fo("kj"), 1.0, Y);
+}
+
+}  // namespace ccpnk

@@ -1,0 +1,59 @@
+// Closed-shell DF-CCSD residual engine (value and tangent programs).
+#pragma once
+
+#include "common.h"
+
+namespace ccpnk {
+
+// A problem resident on the device (the public cc_sys).
+struct System {
+  int o = 0, v = 0, n = 0, P = 0;
+  DBuf<double> f;      // n x n Fock matrix
+  DBuf<double> h;      // n x n one-electron part h = f - (2J - K)[reference density]
+  DBuf<double> fdiag;  // n
+  DBuf<double> Boo, Bov, Bvv;  // [P][o][o], [P][o][v], [P][v][v]
+  DBuf<double> Govov;  // (kc|ld) stored [k][c][l][d]
+  DBuf<double> Lovov;  // 2 (ld|kc) - (lc|kd) stored [l][d][k][c]
+  // eigenbases of the occupied and virtual Fock blocks (filled on demand for A_F^{-1})
+  bool eig_ready = false;
+  std::vector<double> eo, ev;
+  DBuf<double> Uo, Uv;  // column eigenvectors, o x o and v x v
+  size_t namp() const { return (size_t)o * v + (size_t)o * o * v * v; }
+};
+
+void system_init(const Exec& ex, System& s, int o, int v, int P, const double* fock_dev, const double* B_dev);
+
+// Intermediates of one residual evaluation; the tangent program reuses the values.
+class Engine {
+ public:
+  Engine(const Exec& ex, const System& s);
+  // R(t), E(t): t = [t1 | t2] on the device (namp doubles), r = [r1 | r2].
+  // Leaves the intermediates of t in place for later tangent() calls.
+  void value(const double* t, double* r, double* energy_dev, cc_precision prec);
+  // J(t) d at the t of the last value() call.
+  void tangent(const double* d, double* jd, cc_precision prec);
+  const Exec& exec() const { return ex_; }
+  double* scratch() { return scratch_.p; }
+  size_t scratch_count() const { return scratch_.n; }
+
+ private:
+  struct Pair {
+    DBuf<double> val, tan;
+  };
+  void alloc(Pair& x, size_t n);
+  void ladder(const double* Xv, const double* Yv, const double* T, double* R, cc_precision prec);
+  void program(bool tan, cc_precision prec, double* r_out);
+  Exec ex_;
+  const System& s_;
+  int ladder_block_ = 1;
+  Pair t_, u_, Btoo_, Btvv_, Btvo_, gam_, hY_, Ft_, Z_, Wk_, Woo_, Cint_, Dint_, Gv_, Go_, X_, Y2_;
+  DBuf<double> W_;        // ladder workspace, ladder_block_ * v^3
+  DBuf<double> scratch_;  // reduction partials
+};
+
+// y = A_F x on [x1 | x2] vectors (Eq. Preconditioner, App. C)
+void apply_AF(const Exec& ex, const System& s, const double* x, double* y, cc_precision prec);
+// y = (A_F + shift)^{-1} x in the eigenbases of the Fock blocks (exact Sylvester inverse)
+void solve_AF_direct(const Exec& ex, System& s, const double* x, double* y, double shift, double* work);
+
+}  // namespace ccpnk

@@ -1,0 +1,187 @@
+// Shared declarations of the libccpnk CUDA sources (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/ccpnk.h"
+
+namespace ccpnk {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+  int status;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int status, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define CC_CUDA(x) ::ccpnk::cuda_check((x), #x)
+#define CC_REQUIRE(cond, status, msg) \
+  do {                                \
+    if (!(cond)) ::ccpnk::fail((status), (msg)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory: a budgeted pool of cudaMalloc'd blocks, reused by size class
+// ---------------------------------------------------------------------------
+class Pool {
+ public:
+  explicit Pool(size_t budget) : budget_(budget) {}
+  ~Pool();
+  void* get(size_t bytes);
+  void put(void* p);
+  void release_free();  // frees cached blocks
+  size_t held() const { return held_; }
+  size_t budget() const { return budget_; }
+
+ private:
+  struct Block {
+    void* p;
+    size_t bytes;
+    bool used;
+  };
+  std::vector<Block> blocks_;
+  size_t budget_;
+  size_t held_ = 0;
+};
+
+// RAII device buffer from a pool
+template <typename T>
+struct DBuf {
+  Pool* pool = nullptr;
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(Pool* pl, size_t count) { alloc(pl, count); }
+  void alloc(Pool* pl, size_t count) {
+    reset();
+    pool = pl;
+    n = count;
+    p = count ? static_cast<T*>(pl->get(count * sizeof(T))) : nullptr;
+  }
+  void reset() {
+    if (p && pool) pool->put(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DBuf() { reset(); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : pool(o.pool), p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    reset();
+    pool = o.pool; p = o.p; n = o.n;
+    o.p = nullptr; o.n = 0;
+    return *this;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// launch bookkeeping
+// ---------------------------------------------------------------------------
+struct Exec {
+  cudaStream_t stream = nullptr;
+  Pool* pool = nullptr;
+  uint64_t* launches = nullptr;  // incremented for every kernel launch
+  int* dev_flag = nullptr;       // device error flag (bounded waits, bad shapes)
+  int sm_count = 148;
+  void count(uint64_t k = 1) const {
+    if (launches) *launches += k;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// GEMM with compound indices: x -> (x / inner) * s1 + (x % inner) * s2
+// ---------------------------------------------------------------------------
+struct CIdx {
+  int inner;
+  long long s1, s2;
+};
+
+struct GemmArgs {
+  const double* A;
+  const double* B;
+  double* C;
+  int M, N, K, batch;
+  CIdx am, ak, ab;  // A(m, k) of batch b at A + am(m) + ak(k) + ab(b)
+  CIdx bk, bn, bb;  // B(k, n)
+  CIdx cm, cn, cb;  // C(m, n)
+  double alpha, beta;
+  int a_kfast, b_kfast;  // unit stride along k in A / B (picks the coalesced load order)
+};
+
+// Tensor-core GEMM (gemm_tc.cu): same contract as the FP64 kernel, run on tcgen05.
+void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g);
+
+// ---------------------------------------------------------------------------
+// tensors and contractions
+// ---------------------------------------------------------------------------
+constexpr int kMaxModes = 6;
+
+// A strided view of an FP64 device array with one label per mode.
+struct TView {
+  double* p = nullptr;
+  int nd = 0;
+  int ext[kMaxModes] = {0};
+  long long st[kMaxModes] = {0};
+  char lab[kMaxModes + 1] = {0};
+};
+
+// Row-major view: labels like "Pac" and extents.
+TView view(double* p, const char* labels, std::initializer_list<int> ext);
+// View with explicit strides (elements).
+TView view_strided(double* p, const char* labels, std::initializer_list<int> ext,
+                   std::initializer_list<long long> strides);
+
+// C = alpha * contract(A, B) + beta * C over the labels: labels of C present in both A and B
+// are batch modes, labels in A and C the row modes, in B and C the column modes, labels in
+// A and B only are summed. prec selects the FP64 FMA kernel or the tensor-core kernel.
+void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
+              double beta, const TView& C);
+
+// ---------------------------------------------------------------------------
+// kernels with host launchers (elementwise.cu)
+// ---------------------------------------------------------------------------
+void k_axpby(const Exec& ex, size_t n, double a, const double* x, double b, double* y);  // y = a x + b y
+void k_scale(const Exec& ex, size_t n, double a, double* y);
+void k_fill(const Exec& ex, size_t n, double val, double* y);
+void k_copy(const Exec& ex, size_t n, const double* x, double* y);
+// out[i][j][a][b] (+)= X[i][j][a][b] + X[j][i][b][a]
+void k_sym_add(const Exec& ex, int o, int v, const double* X, double* out, double beta);
+// u[i][j][a][b] = 2 t[i][j][a][b] - t[j][i][a][b]
+void k_make_u(const Exec& ex, int o, int v, const double* t, double* u);
+// L[p][q][r][s] = 2 g[p][q][r][s] - g[p][s][r][q] over an (o v o v) block
+void k_make_L_ovov(const Exec& ex, int o, int v, const double* g, double* L);
+// gamma[P] = sum_k A[P][k][k]
+void k_trace_batched(const Exec& ex, int P, int m, const double* A, double* gamma);
+// Deterministic reductions: result written to a device scalar.
+void k_dot(const Exec& ex, size_t n, const double* x, const double* y, double* out, double* scratch);
+// out[k] = dot(Q[k], w) for k < m (rows of length n), deterministic.
+void k_multi_dot(const Exec& ex, int m, size_t n, const double* Q, size_t ldq, const double* w,
+                 double* out, double* scratch);
+// w -= sum_k h[k] Q[k]  (h on device)
+void k_multi_axpy(const Exec& ex, int m, size_t n, const double* Q, size_t ldq, const double* h,
+                  double* w);
+// energy terms: E = sum (2 g_iajb - g_ibja)(t2_ijab + t1_ia t1_jb) + 2 sum f_ia t1_ia
+void k_energy(const Exec& ex, int o, int v, const double* govov, const double* t1, const double* t2,
+              const double* fov, int ldf, double* out, double* scratch);
+// scaled elementwise divide: y = x / (D + shift) with D built from diagonal Fock entries
+void k_denom_divide(const Exec& ex, int o, int v, const double* fdiag, double shift,
+                    const double* x1, const double* x2, double* y1, double* y2, double scale);
+// copy a (rows x cols) block with strides
+void k_copy2d(const Exec& ex, int rows, int cols, const double* src, long long lds, double* dst,
+              long long ldd);
+// checks |B[P][p][q] - B[P][q][p]| <= tol * max|B|; writes the max asymmetry to out
+void k_asym(const Exec& ex, int P, int n, const double* B, double* out, double* scratch);
+
+// FP32 staging for tensor-core contractions (elementwise.cu)
+void k_to_f32(const Exec& ex, size_t n, const double* x, float* y);
+
+}  // namespace ccpnk
