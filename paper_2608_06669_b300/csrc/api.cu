@@ -15,6 +15,7 @@ struct cc_ctx {
   std::unique_ptr<ccpnk::Pool> pool;
   uint64_t launches = 0;
   int sm_count = 148;
+  int* dflag = nullptr;  // device error flag written by bounded waits
   std::string err;
   ccpnk::Exec ex() {
     ccpnk::Exec e;
@@ -22,6 +23,7 @@ struct cc_ctx {
     e.pool = pool.get();
     e.launches = &launches;
     e.sm_count = sm_count;
+    e.dev_flag = dflag;
     return e;
   }
 };
@@ -107,11 +109,26 @@ using namespace ccpnk;
 
 namespace {
 
+// Reads and clears the device error flag after the context's work has completed.
+void check_device_flag(cc_ctx* ctx) {
+  if (!ctx || !ctx->dflag) return;
+  int h = 0;
+  CC_CUDA(cudaMemcpyAsync(&h, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CC_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    CC_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    fail(CC_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+  }
+}
+
 template <typename F>
 int guarded(cc_ctx* ctx, F&& f) {
   try {
     if (ctx) CC_CUDA(cudaSetDevice(ctx->device));
-    return f();
+    int st = f();
+    check_device_flag(ctx);
+    return st;
   } catch (const Error& e) {
     if (ctx) ctx->err = e.msg;
     return e.status;
@@ -207,6 +224,9 @@ int cc_ctx_create(cc_ctx** out, int device, size_t mem_budget, void* stream) {
       c->own_stream = true;
     }
     c->pool.reset(new Pool(mem_budget));
+    CC_CUDA(cudaMalloc(&c->dflag, sizeof(int)));
+    CC_CUDA(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
+    CC_CUDA(cudaStreamSynchronize(c->stream));
     return CC_OK;
   });
   if (st == CC_OK) *out = c.release();
@@ -218,6 +238,7 @@ void cc_ctx_destroy(cc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   ctx->pool.reset();
+  if (ctx->dflag) cudaFree(ctx->dflag);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

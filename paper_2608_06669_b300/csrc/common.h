@@ -98,11 +98,12 @@ struct Exec {
 };
 
 // ---------------------------------------------------------------------------
-// GEMM with compound indices: x -> (x / inner) * s1 + (x % inner) * s2
+// GEMM with compound indices of up to three strided modes:
+//   x = (i0 * e1 + i1) * e2 + i2  ->  offset i0 * s0 + i1 * s1 + i2 * s2
 // ---------------------------------------------------------------------------
 struct CIdx {
-  int inner;
-  long long s1, s2;
+  int e1 = 1, e2 = 1;
+  long long s0 = 0, s1 = 0, s2 = 0;
 };
 
 struct GemmArgs {
@@ -115,6 +116,9 @@ struct GemmArgs {
   CIdx cm, cn, cb;  // C(m, n)
   double alpha, beta;
   int a_kfast, b_kfast;  // unit stride along k in A / B (picks the coalesced load order)
+  int splits;            // split-K factor (1: write C directly)
+  int kchunk;            // k range per split (multiple of the k slice)
+  double* part;          // split-K partials [splits][batch][M][N]
 };
 
 // Tensor-core GEMM (gemm_tc.cu): same contract as the FP64 kernel, run on tcgen05.

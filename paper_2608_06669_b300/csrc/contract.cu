@@ -2,12 +2,12 @@
 //
 // Every term of the CCSD residual, of its linearisation and of the A_F operator is a
 // contraction of two tensors over shared labels. The planner below maps a contraction onto
-// one GEMM whose row, column, sum and batch indices are each a compound of at most two
+// one GEMM whose row, column, sum and batch indices are each a compound of up to three
 // strided modes (after merging modes that are contiguous in every operand), so permuted
-// layouts are read in place with no transpose copies. Groups with more modes are split into
-// a host loop. The FP64 kernel runs on the FMA pipe (there is no FP64 tensor-core kind of
-// tcgen05.mma); tensor-core precisions gather their operands into K-major FP32 staging
-// buffers and run the tcgen05 kernel (gemm_tc.cu).
+// layouts are read in place with no transpose copies. Contractions with few output tiles and
+// a long sum are split along k over extra blocks whose partial sums are added in a fixed
+// order afterwards (deterministic results). The FP64 kernel runs on the FMA pipe (tcgen05.mma
+// has no FP64 kind); tensor-core precisions go to gemm_tc.cu.
 #include <algorithm>
 #include <cstring>
 
@@ -43,30 +43,34 @@ TView view_strided(double* p, const char* labels, std::initializer_list<int> ext
 
 // ---------------------------------------------------------------------------
 // FP64 kernel: 64 x 64 output tile, 16-deep k slices staged in shared memory,
-// 256 threads each holding a 4 x 4 accumulator block.
+// 256 threads each holding a 4 x 4 accumulator block, two blocks per SM.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 __device__ __forceinline__ long long cidx(const CIdx& c, int x) {
-  if (c.inner == 1) return (long long)x * c.s1;
-  int q = x / c.inner;
-  int r = x - q * c.inner;
-  return (long long)q * c.s1 + (long long)r * c.s2;
+  if (c.e1 == 1 && c.e2 == 1) return (long long)x * c.s0;
+  int i2 = x % c.e2;
+  int r = x / c.e2;
+  int i1 = r % c.e1;
+  int i0 = r / c.e1;
+  return (long long)i0 * c.s0 + (long long)i1 * c.s1 + (long long)i2 * c.s2;
 }
 
-__global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmArgs g) {
+__global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int split = blockIdx.z % g.splits;
+  const int kbeg = split * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
 
   // per-thread load coordinates (fixed across k slices)
   int a_mm[4], a_kk[4], b_nn[4], b_kk[4];
   long long a_moff[4], b_noff[4];
-  bool a_mok[4], b_nok[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     int e = tid + NT * r;
@@ -75,29 +79,26 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmArgs g) {
     if (g.b_kfast) { b_kk[r] = e % BK; b_nn[r] = e / BK; }
     else           { b_nn[r] = e % BN; b_kk[r] = e / BN; }
     int m = m0 + a_mm[r], n = n0 + b_nn[r];
-    a_mok[r] = m < g.M;
-    b_nok[r] = n < g.N;
-    a_moff[r] = a_mok[r] ? cidx(g.am, m) : 0;
-    b_noff[r] = b_nok[r] ? cidx(g.bn, n) : 0;
+    a_moff[r] = m < g.M ? cidx(g.am, m) : -1;
+    b_noff[r] = n < g.N ? cidx(g.bn, n) : -1;
   }
 
-  for (int bz = blockIdx.z; bz < g.batch; bz += gridDim.z) {
+  for (int bz = blockIdx.z / g.splits; bz < g.batch; bz += gridDim.z / g.splits) {
     const double* A = g.A + cidx(g.ab, bz);
     const double* B = g.B + cidx(g.bb, bz);
-    double* C = g.C + cidx(g.cb, bz);
     double acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         int k = k0 + a_kk[r];
-        As[a_kk[r]][a_mm[r]] = (a_mok[r] && k < g.K) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0;
+        As[a_kk[r]][a_mm[r]] = (a_moff[r] >= 0 && k < kend) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0;
         int kb = k0 + b_kk[r];
-        Bs[b_kk[r]][b_nn[r]] = (b_nok[r] && kb < g.K) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0;
+        Bs[b_kk[r]][b_nn[r]] = (b_noff[r] >= 0 && kb < kend) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0;
       }
       __syncthreads();
 #pragma unroll
@@ -114,6 +115,22 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmArgs g) {
       }
       __syncthreads();
     }
+    if (g.splits > 1) {
+      // partials [split][batch][M][N]
+      double* P = g.part + ((size_t)split * g.batch + bz) * (size_t)g.M * g.N;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int n = n0 + tx + 16 * j;
+          if (n < g.N) P[(size_t)m * g.N + n] = acc[i][j];
+        }
+      }
+      continue;
+    }
+    double* C = g.C + cidx(g.cb, bz);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       int m = m0 + ty + 16 * i;
@@ -129,6 +146,24 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmArgs g) {
         *c = val;
       }
     }
+  }
+}
+
+// C = alpha * sum_s part[s] + beta * C, the splits added in order
+__global__ void splitk_reduce_kernel(GemmArgs g) {
+  const size_t per = (size_t)g.M * g.N;
+  const size_t tot = per * g.batch;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    int n = (int)(e % g.N);
+    size_t r = e / g.N;
+    int m = (int)(r % g.M);
+    int b = (int)(r / g.M);
+    double s = 0.0;
+    for (int q = 0; q < g.splits; ++q) s += g.part[(size_t)q * tot + e];
+    double* c = g.C + cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
+    double val = g.alpha * s;
+    if (g.beta != 0.0) val = fma(g.beta, *c, val);
+    *c = val;
   }
 }
 
@@ -161,18 +196,25 @@ void merge_modes(std::vector<Mode>& g, bool inA, bool inB, bool inC) {
   }
 }
 
+// compound index of up to three modes (outermost first)
 CIdx make_cidx(const std::vector<Mode>& g, int which) {
-  CIdx c{1, 0, 0};
+  CIdx c;
   auto s = [&](const Mode& m) { return which == 0 ? m.sa : which == 1 ? m.sb : m.sc; };
   if (g.empty()) return c;
   if (g.size() == 1) {
-    c.inner = 1;
-    c.s1 = s(g[0]);
-    return c;
+    c.s0 = s(g[0]);
+  } else if (g.size() == 2) {
+    c.e1 = 1;
+    c.e2 = g[1].ext;
+    c.s0 = s(g[0]);
+    c.s2 = s(g[1]);
+  } else {
+    c.e1 = g[1].ext;
+    c.e2 = g[2].ext;
+    c.s0 = s(g[0]);
+    c.s1 = s(g[1]);
+    c.s2 = s(g[2]);
   }
-  c.inner = g[1].ext;
-  c.s1 = s(g[0]);
-  c.s2 = s(g[1]);
   return c;
 }
 
@@ -182,17 +224,44 @@ long long group_size(const std::vector<Mode>& g) {
   return n;
 }
 
-void launch_gemm(const Exec& ex, cc_precision prec, const GemmArgs& g) {
+long long inner_stride(const CIdx& c) { return (c.e1 == 1 && c.e2 == 1) ? c.s0 : c.s2; }
+
+void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
-  if (prec == CC_FP64) {
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, std::min(g.batch, 65535));
-    CC_REQUIRE(grid.y <= 65535, CC_ERR_INVALID, "gemm: M too large for the grid");
-    gemm_f64_kernel<<<grid, NT, 0, ex.stream>>>(g);
+  if (prec != CC_FP64) {
+    gemm_tc(ex, prec, g);
+    return;
+  }
+  const long long tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
+  CC_REQUIRE(tm <= 65535, CC_ERR_INVALID, "gemm: M too large for the grid");
+  const long long tiles = tm * tn * g.batch;
+  const long long target = 4LL * ex.sm_count;  // two resident blocks per SM, two waves
+  const int ksteps = (g.K + BK - 1) / BK;
+  int splits = 1;
+  if (tiles < target && ksteps >= 8) {
+    splits = (int)std::min<long long>((target + tiles - 1) / tiles, ksteps / 4);
+    splits = std::max(splits, 1);
+  }
+  DBuf<double> part;
+  g.splits = splits;
+  g.kchunk = ((ksteps + splits - 1) / splits) * BK;
+  if (splits > 1) {
+    part.alloc(ex.pool, (size_t)splits * g.batch * g.M * g.N);
+    g.part = part.p;
+  }
+  long long zb = std::min<long long>(g.batch, std::max<long long>(1, 65535 / splits));
+  dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)(zb * splits));
+  gemm_f64_kernel<<<grid, NT, 0, ex.stream>>>(g);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+  if (splits > 1) {
+    size_t tot = (size_t)g.batch * g.M * g.N;
+    int blocks = (int)std::min<size_t>((tot + 255) / 256, (size_t)ex.sm_count * 8);
+    splitk_reduce_kernel<<<blocks, 256, 0, ex.stream>>>(g);
     ex.count();
     CC_CUDA(cudaGetLastError());
-  } else {
-    gemm_tc(ex, prec, g);
   }
+  // part returns to the pool here; later launches on the same stream are ordered after the reduce
 }
 
 }  // namespace
@@ -211,10 +280,11 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
     Mode m{l, C.ext[d], ia >= 0 ? A.st[ia] : 0, ib >= 0 ? B.st[ib] : 0, C.st[d]};
     if (ia >= 0) CC_REQUIRE(A.ext[ia] == C.ext[d], CC_ERR_INVALID, std::string("contract: extent of ") + l);
     if (ib >= 0) CC_REQUIRE(B.ext[ib] == C.ext[d], CC_ERR_INVALID, std::string("contract: extent of ") + l);
+    if (ia < 0 && ib < 0) fail(CC_ERR_INVALID, std::string("contract: output label only in C: ") + l);
+    if (C.ext[d] == 1) continue;
     if (ia >= 0 && ib >= 0) gb.push_back(m);
     else if (ia >= 0) gm.push_back(m);
-    else if (ib >= 0) gn.push_back(m);
-    else fail(CC_ERR_INVALID, std::string("contract: output label only in C: ") + l);
+    else gn.push_back(m);
   }
   for (int d = 0; d < A.nd; ++d) {
     char l = A.lab[d];
@@ -222,6 +292,7 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
     int ib = find(B, l);
     CC_REQUIRE(ib >= 0, CC_ERR_INVALID, std::string("contract: label summed in A only: ") + l);
     CC_REQUIRE(B.ext[ib] == A.ext[d], CC_ERR_INVALID, std::string("contract: extent of ") + l);
+    if (A.ext[d] == 1) continue;
     gk.push_back(Mode{l, A.ext[d], A.st[d], B.st[ib], 0});
   }
   for (int d = 0; d < B.nd; ++d) {
@@ -229,32 +300,36 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
     CC_REQUIRE(find(C, l) >= 0 || find(A, l) >= 0, CC_ERR_INVALID,
                std::string("contract: label summed in B only: ") + l);
   }
+  for (auto* g : {&gb, &gm, &gn})
+    for (auto& m : *g)
+      if (m.ext == 0) return;  // empty output
+  bool empty_sum = false;
+  for (auto& m : gk)
+    if (m.ext == 0) empty_sum = true;
+  if (empty_sum) gk.clear();  // C = beta C (K = 0 below)
+
   merge_modes(gb, true, true, true);
   merge_modes(gm, true, false, true);
   merge_modes(gn, false, true, true);
   merge_modes(gk, true, true, false);
-
-  // modes beyond two per group go to a host loop (outermost first)
+  // row or column modes beyond three become batch modes (offsets in their operands only)
+  while (gm.size() > 3) { gb.insert(gb.begin(), gm.front()); gm.erase(gm.begin()); }
+  while (gn.size() > 3) { gb.insert(gb.begin(), gn.front()); gn.erase(gn.begin()); }
+  // modes beyond three per group go to a host loop (outermost first)
   std::vector<Mode> loops;
   auto spill = [&](std::vector<Mode>& g) {
-    while (g.size() > 2) {
+    while (g.size() > 3) {
       loops.push_back(g.front());
       g.erase(g.begin());
     }
   };
   spill(gb);
-  spill(gm);
-  spill(gn);
   spill(gk);
-  for (auto* g : {&gm, &gn, &gk, &gb})
-    for (auto& m : *g) if (m.ext == 0) return;  // empty contraction output or sum
-  for (auto& m : loops)
-    if (m.ext == 0) return;
 
   GemmArgs g{};
   g.M = (int)group_size(gm);
   g.N = (int)group_size(gn);
-  g.K = (int)group_size(gk);
+  g.K = empty_sum ? 0 : (int)group_size(gk);
   g.batch = (int)group_size(gb);
   g.am = make_cidx(gm, 0);
   g.ak = make_cidx(gk, 0);
@@ -267,11 +342,10 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
   g.cb = make_cidx(gb, 2);
   g.alpha = alpha;
   g.beta = beta;
-  auto inner_stride = [](const CIdx& c) { return c.inner == 1 ? c.s1 : c.s2; };
+  g.splits = 1;
   g.a_kfast = gk.empty() ? 1 : (inner_stride(g.ak) == 1);
   g.b_kfast = gk.empty() ? 1 : (inner_stride(g.bk) == 1 && inner_stride(g.bn) != 1);
 
-  // host loop over spilled modes
   const int nl = (int)loops.size();
   std::vector<int> idx(nl, 0);
   while (true) {

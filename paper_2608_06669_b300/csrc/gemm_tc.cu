@@ -1,11 +1,331 @@
-// Tensor-core GEMM on tcgen05 (placeholder until the kernel lands).
+// Tensor-core contractions on sm_103a: tcgen05.mma (kind::tf32, FP32 accumulation in TMEM),
+// operands brought into 128-byte-swizzled shared memory by TMA through a multi-stage mbarrier
+// pipeline, one elected thread issuing the MMAs, and an epilogue that reads the accumulator
+// with tcgen05.ld and applies C = alpha * acc + beta * C in FP64.
+//
+// The compound-index operands of a contraction are first gathered into K-major FP32 staging
+// buffers (rounded to TF32 to nearest, padded to whole tiles with zeros), so the tensor-core
+// kernel sees plain [batch][rows][k] arrays that TMA can tile. Every wait on an mbarrier is
+// bounded by the global timer; a timeout sets the context's error flag and the kernel leaves
+// after releasing its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "common.h"
 
 namespace ccpnk {
+namespace {
+
+constexpr int TM = 128;         // tile rows = UMMA M
+constexpr int TN = 128;         // tile columns = UMMA N
+constexpr int TK = 32;          // k per pipeline stage: 32 FP32 = one 128-byte swizzle row
+constexpr int UK = 8;           // k per tcgen05.mma of kind::tf32
+constexpr int STAGES = 4;
+constexpr int THREADS = 128;    // four warps: TMA producer, MMA issuer, all four in the epilogue
+constexpr uint32_t A_BYTES = TM * TK * 4;
+constexpr uint32_t B_BYTES = TN * TK * 4;
+constexpr uint32_t TMEM_COLS = TN;  // FP32 accumulator columns
+constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s bound on any wait
+
+__device__ __forceinline__ long long cidx(const CIdx& c, int x) {
+  if (c.e1 == 1 && c.e2 == 1) return (long long)x * c.s0;
+  int i2 = x % c.e2;
+  int r = x / c.e2;
+  int i1 = r % c.e1;
+  int i0 = r / c.e1;
+  return (long long)i0 * c.s0 + (long long)i1 * c.s1 + (long long)i2 * c.s2;
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// out[b][r][k] for r < rows_pad, k < k_pad (FP32, TF32-rounded), zero outside rows x K
+__global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
+                              int batch, int rows_pad, int k_pad, float* __restrict__ out) {
+  const size_t tot = (size_t)batch * rows_pad * k_pad;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    int k = (int)(e % k_pad);
+    size_t q = e / k_pad;
+    int r = (int)(q % rows_pad);
+    int b = (int)(q / rows_pad);
+    float v = 0.0f;
+    if (r < rows && k < K) v = to_tf32((float)src[cidx(bix, b) + cidx(rix, r) + cidx(kix, k)]);
+    out[e] = v;
+  }
+}
+
+__global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
+  const size_t tot = (size_t)g.batch * g.M * g.N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    int n = (int)(e % g.N);
+    size_t r = e / g.N;
+    int m = (int)(r % g.M);
+    int b = (int)(r / g.M);
+    double* c = g.C + cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
+    *c = g.beta == 0.0 ? 0.0 : g.beta * *c;
+  }
+}
+
+struct TcArgs {
+  int M, N, kblocks;
+  CIdx cm, cn, cb;
+  double alpha, beta;
+  double* C;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// waits for the phase of the given parity to complete; false after WAIT_NS
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 0) {
+      unsigned long long t = gtime();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > WAIT_NS) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, N = TN, M = TM
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = (uint64_t*)(sB + STAGES * B_BYTES);  // full[STAGES], empty[STAGES], done
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN, bz = blockIdx.z;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < g.kblocks; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(empty0 + 8 * s, ph ^ 1)) { ok = false; break; }
+      mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
+      tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, kb * TK, m0, bz);
+      tma_load_3d(smem_u32(sB + s * B_BYTES), &tmB, full0 + 8 * s, kb * TK, n0, bz);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kb = 0; kb < g.kblocks; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(full0 + 8 * s, ph)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+      for (int j = 0; j < TK / UK; ++j) {
+        const uint64_t da = sdesc(a0 + j * UK * 4), db = sdesc(b0 + j * UK * 4);
+        const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(IDESC), "r"(acc)
+            : "memory");
+      }
+      // frees the stage once these MMAs have read it
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done) : "memory");
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
+  if (!mbar_wait(done, 0)) ok = false;
+  ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective: decide per warp
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    const long long crow = row < g.M ? cidx(g.cb, bz) + cidx(g.cm, row) : 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%"
+          "22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+            "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+            "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+            "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < g.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < g.N) {
+            double* c = g.C + crow + cidx(g.cn, n);
+            double val = g.alpha * (double)__uint_as_float(r[j]);
+            if (g.beta != 0.0) val = fma(g.beta, *c, val);
+            *c = val;
+          }
+        }
+      }
+    }
+  }
+  if (warp == 0 && lane == 0) {
+    // never leave with copies in flight: the last loads issued must have landed (bounded)
+    for (int kb = std::max(0, g.kblocks - STAGES); kb < g.kblocks; ++kb)
+      if (!mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1)) ok = false;
+  }
+  if (!ok && lane == 0) atomicExch(g.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CC_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    CC_REQUIRE(p && q == cudaDriverEntryPointSuccess, CC_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 3-D map over a [batch][rows][k_pad] FP32 array, box = 32 (k) x box_rows x 1
+CUtensorMap make_map(const float* base, int k_pad, int rows_pad, int batch, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)k_pad * 4, (cuuint64_t)k_pad * rows_pad * 4};
+  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CC_REQUIRE(r == CUDA_SUCCESS, CC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+constexpr size_t SMEM_BYTES = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 1) * 8 + 16;
+
+}  // namespace
 
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g) {
-  (void)ex; (void)prec; (void)g;
-  fail(CC_ERR_INVALID, "tensor-core contractions are not available in this build");
+  CC_REQUIRE(prec == CC_MIXED_TF32, CC_ERR_INVALID, "tensor-core precision not available");
+  CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
+  if (g.K <= 0) {
+    int blocks = (int)std::min<size_t>(((size_t)g.batch * g.M * g.N + 255) / 256, (size_t)ex.sm_count * 8);
+    scale_c_kernel<<<std::max(blocks, 1), 256, 0, ex.stream>>>(g);
+    ex.count();
+    CC_CUDA(cudaGetLastError());
+    return;
+  }
+  CC_REQUIRE(g.batch <= 65535, CC_ERR_INVALID, "tensor-core contraction: batch too large");
+  const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
+  const int k_pad = (g.K + TK - 1) / TK * TK;
+  const size_t nA = (size_t)g.batch * rowsA * k_pad, nB = (size_t)g.batch * rowsB * k_pad;
+  DBuf<double> stA(ex.pool, (nA + 1) / 2), stB(ex.pool, (nB + 1) / 2);
+  float* fA = reinterpret_cast<float*>(stA.p);
+  float* fB = reinterpret_cast<float*>(stB.p);
+  auto blocks_for = [&](size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)ex.sm_count * 16)); };
+  gather_kernel<<<blocks_for(nA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, fA);
+  ex.count();
+  gather_kernel<<<blocks_for(nB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad, fB);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+  CUtensorMap mA = make_map(fA, k_pad, rowsA, g.batch, TM);
+  CUtensorMap mB = make_map(fB, k_pad, rowsB, g.batch, TN);
+  TcArgs a;
+  a.M = g.M;
+  a.N = g.N;
+  a.kblocks = k_pad / TK;
+  a.cm = g.cm;
+  a.cn = g.cn;
+  a.cb = g.cb;
+  a.alpha = g.alpha;
+  a.beta = g.beta;
+  a.C = g.C;
+  a.err = ex.dev_flag;
+  static bool attr = false;
+  if (!attr) {
+    CC_CUDA(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    attr = true;
+  }
+  dim3 grid(rowsB / TN, rowsA / TM, g.batch);
+  gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
 }
 
 }  // namespace ccpnk

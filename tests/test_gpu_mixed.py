@@ -1,0 +1,95 @@
+"""Mixed precision: tcgen05 TF32 contractions (FP32 accumulation) against the FP64 oracle.
+
+TF32 keeps 10 explicit mantissa bits, so each product carries a relative error near 2^-11
+and a contraction of K terms an error near 2^-11 * sum|a b|. The tests bound the error
+normwise (max element error over the largest oracle element); the solver keeps its outer
+residual, energy and update in FP64, so a mixed-precision solve still lands on the FP64 root
+to 1e-8 Eh.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dfccsd as cc
+from paper_2608_06669_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "energies.json")
+TF32_TOL = 5e-3
+
+
+def nrel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_device):
+    from paper_2608_06669_b300 import ccpnk
+
+    c = ccpnk.Context(0)
+    yield c
+    c.close()
+
+
+def gsys(ctx, s):
+    from paper_2608_06669_b300 import ccpnk
+
+    return ccpnk.System.from_synth(ctx, s)
+
+
+@pytest.mark.parametrize("o,v,gauge", [(1, 1, "canonical"), (3, 7, "haar"), (6, 40, "small"), (10, 90, "small")])
+def test_tf32_AF_apply(ctx, o, v, gauge):
+    s = synth.make_system(o, v, 4, seed=3, gauge=gauge)
+    x1, x2 = synth.random_amplitudes(np.random.default_rng(1), o, v, 1.0, 1.0)
+    y1, y2 = gsys(ctx, s).apply_AF(x1, x2, 0, prec="tf32")
+    q1, q2 = cc.apply_AF(s.fock, o, x1, x2)
+    assert nrel(y1, q1) < 2e-3 and nrel(y2, q2) < 2e-3
+
+
+@pytest.mark.parametrize("o,v,naux,gauge", [(2, 4, 5, "haar"), (4, 9, 11, "small"), (7, 33, 20, "haar")])
+def test_tf32_residual_and_jvp(ctx, o, v, naux, gauge):
+    s = synth.make_system(o, v, naux, seed=7 + o, gauge=gauge)
+    rng = np.random.default_rng(o * v)
+    t1, t2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    d1, d2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    g = gsys(ctx, s)
+    r1, r2, e = g.residual(t1, t2, prec="tf32")
+    q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
+    scale = max(np.abs(q1).max(), np.abs(q2).max())
+    assert np.abs(r2 - q2).max() < TF32_TOL * scale and np.abs(r1 - q1).max() < TF32_TOL * scale
+    j1, j2 = g.jvp(t1, t2, d1, d2, prec="tf32")
+    p1, p2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+    scale = max(np.abs(p1).max(), np.abs(p2).max())
+    assert np.abs(j2 - p2).max() < TF32_TOL * scale and np.abs(j1 - p1).max() < TF32_TOL * scale
+
+
+def test_tf32_jvp_workload_error(ctx):
+    """The error of the TF32 JVP on the o=10, v=90 workload, stated against the FP64 oracle."""
+    s = synth.workload("o10v90_rotated")
+    o, v = s.o, s.v
+    t1, t2 = cc.mp2_guess(s.fock, s.B, o)
+    d1, d2 = synth.random_amplitudes(np.random.default_rng(4), o, v, 0.01, 0.01)
+    j1, j2 = gsys(ctx, s).jvp(t1, t2, d1, d2, prec="tf32")
+    p1, p2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+    err = max(nrel(j1, p1) * np.abs(p1).max(), np.abs(j2 - p2).max()) / max(np.abs(p1).max(), np.abs(p2).max())
+    assert err < TF32_TOL
+
+
+@pytest.mark.parametrize("method", ["pnk", "nk"])
+def test_mixed_solve_reaches_fp64_root(ctx, method):
+    s = synth.workload("o5v20_canonical")
+    ref = json.load(open(GOLDEN))["o5v20_canonical"]["e_corr"]
+    _, _, rep = gsys(ctx, s).solve(method, "tf32")
+    assert rep["status_code"] == 0, rep
+    assert rep["res_norm"] < 1e-8 and abs(rep["energy"] - ref) < 1e-8
+
+
+def test_mixed_pnk_workload(ctx):
+    s = synth.workload("o10v90_rotated")
+    ref = json.load(open(GOLDEN))["o10v90_rotated"]["e_corr"]
+    _, _, rep = gsys(ctx, s).solve("pnk", "tf32")
+    assert rep["status_code"] == 0, rep
+    assert abs(rep["energy"] - ref) < 1e-8
