@@ -107,6 +107,14 @@ const char* cc_last_error(const cc_ctx* ctx);
 size_t cc_ctx_device_bytes(const cc_ctx* ctx);
 /* Number of kernel launches the context has issued since it was created. */
 uint64_t cc_ctx_launches(const cc_ctx* ctx);
+/* Kernel timer (tracing): enable != 0 clears the records and brackets every tagged launch
+ * with CUDA events on the context's stream; enable = 0 turns it off. Tags in use:
+ * "ladder_build.<p>" and "ladder_contract.<p>" (the two GEMMs of the particle-particle
+ * ladder, <p> = fp64 or tf32). */
+int cc_ctx_profile(cc_ctx* ctx, int enable);
+/* Launch count, summed event time (ms) and summed algorithmic flops of one tag since the
+ * last cc_ctx_profile(ctx, 1). Waits for the recorded launches to finish. */
+int cc_ctx_profile_get(cc_ctx* ctx, const char* tag, uint64_t* launches, double* total_ms, double* flops);
 
 /* A problem resident on the device: copies fock (n x n) and B (naux x n x n), host or device. */
 int cc_sys_create(cc_ctx* ctx, int o, int v, int naux, const double* fock, const double* B, cc_sys** out);

@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
             "cc_last_error": (ctypes.c_char_p, [vp]),
             "cc_ctx_device_bytes": (sz, [vp]),
             "cc_ctx_launches": (u64, [vp]),
+            "cc_ctx_profile": (i, [vp, i]),
+            "cc_ctx_profile_get": (i, [vp, ctypes.c_char_p, ctypes.POINTER(u64), ctypes.POINTER(d), ctypes.POINTER(d)]),
             "cc_sys_create": (i, [vp, i, i, i, vp, vp, pp]),
             "cc_sys_destroy": (None, [vp]),
             "cc_residual": (i, [vp, vp, vp, vp, vp, vp, ctypes.POINTER(d), i]),
@@ -158,6 +160,17 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().cc_ctx_launches(self.h))
+
+    def profile(self, enable: bool = True):
+        """Turns the tagged kernel timer on (clearing its records) or off."""
+        _check(self.h, lib().cc_ctx_profile(self.h, int(enable)))
+
+    def profile_get(self, tag: str):
+        """(launches, total_ms, flops) recorded for a tag since profile(True)."""
+        n, ms, fl = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+        _check(self.h, lib().cc_ctx_profile_get(self.h, tag.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                                ctypes.byref(fl)))
+        return int(n.value), float(ms.value), float(fl.value)
 
     def close(self):
         if getattr(self, "h", None):

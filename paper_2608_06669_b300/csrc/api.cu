@@ -17,6 +17,7 @@ struct cc_ctx {
   int sm_count = 148;
   int* dflag = nullptr;  // device error flag written by bounded waits
   std::string err;
+  ccpnk::Prof prof;
   ccpnk::Exec ex() {
     ccpnk::Exec e;
     e.stream = stream;
@@ -24,6 +25,7 @@ struct cc_ctx {
     e.launches = &launches;
     e.sm_count = sm_count;
     e.dev_flag = dflag;
+    e.prof = &prof;
     return e;
   }
 };
@@ -89,6 +91,48 @@ void Pool::put(void* p) {
       b.used = false;
       return;
     }
+}
+
+void Exec::mark_begin(cudaEvent_t* a) const {
+  CC_CUDA(cudaEventCreate(a));
+  CC_CUDA(cudaEventRecord(*a, stream));
+}
+
+void Exec::mark_end(const char* tag, cudaEvent_t a, double flops) const {
+  cudaEvent_t b;
+  CC_CUDA(cudaEventCreate(&b));
+  CC_CUDA(cudaEventRecord(b, stream));
+  prof->pending.push_back({tag, a, b, flops});
+}
+
+void Prof::resolve() {
+  for (auto& r : pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    Sum* s = nullptr;
+    for (auto& d : done)
+      if (d.first == r.tag) s = &d.second;
+    if (!s) {
+      done.push_back({r.tag, Sum{}});
+      s = &done.back().second;
+    }
+    s->launches += 1;
+    s->ms += ms;
+    s->flops += r.flops;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  pending.clear();
+}
+
+void Prof::reset() {
+  for (auto& r : pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  pending.clear();
+  done.clear();
 }
 
 void Pool::release_free() {
@@ -248,6 +292,35 @@ const char* cc_last_error(const cc_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 size_t cc_ctx_device_bytes(const cc_ctx* ctx) { return ctx && ctx->pool ? ctx->pool->held() : 0; }
 
 uint64_t cc_ctx_launches(const cc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int cc_ctx_profile(cc_ctx* ctx, int enable) {
+  if (!ctx) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->prof.reset();
+    ctx->prof.on = enable != 0;
+    return CC_OK;
+  });
+}
+
+int cc_ctx_profile_get(cc_ctx* ctx, const char* tag, uint64_t* launches, double* total_ms, double* flops) {
+  if (!ctx || !tag) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    ctx->prof.resolve();
+    uint64_t l = 0;
+    double ms = 0.0, fl = 0.0;
+    for (auto& d : ctx->prof.done)
+      if (d.first == tag) {
+        l = d.second.launches;
+        ms = d.second.ms;
+        fl = d.second.flops;
+      }
+    if (launches) *launches = l;
+    if (total_ms) *total_ms = ms;
+    if (flops) *flops = fl;
+    return CC_OK;
+  });
+}
 
 int cc_sys_create(cc_ctx* ctx, int o, int v, int naux, const double* fock, const double* B, cc_sys** out) {
   if (!ctx || !out) return CC_ERR_INVALID;

@@ -112,9 +112,11 @@ void Engine::ladder(const double* Xv, const double* Yv, const double* T, double*
     const int al = std::min(ladder_block_, v - a0);
     TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {P, al, v}, {(long long)v * v, v, 1});
     TView W = view(W_.p, "abcd", {al, v, v, v});
-    contract(ex_, prec, 1.0, Xa, view(Y, "Pbd", {P, v, v}), 0.0, W);
+    const bool f64 = prec == CC_FP64;
+    contract(ex_, prec, 1.0, Xa, view(Y, "Pbd", {P, v, v}), 0.0, W, f64 ? "ladder_build.fp64" : "ladder_build.tf32");
     TView Rv = view_strided(R + (size_t)a0 * v, "ijab", {o, o, al, v}, {(long long)o * v * v, (long long)v * v, v, 1});
-    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 1.0, Rv);
+    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 1.0, Rv,
+             f64 ? "ladder_contract.fp64" : "ladder_contract.tf32");
   }
 }
 

@@ -84,6 +84,27 @@ struct DBuf {
 };
 
 // ---------------------------------------------------------------------------
+// kernel timer: CUDA events around tagged launches, resolved on request
+// ---------------------------------------------------------------------------
+struct Prof {
+  struct Rec {
+    std::string tag;
+    cudaEvent_t a, b;
+    double flops;
+  };
+  struct Sum {
+    uint64_t launches = 0;
+    double ms = 0.0, flops = 0.0;
+  };
+  bool on = false;
+  std::vector<Rec> pending;
+  std::vector<std::pair<std::string, Sum>> done;
+  void resolve();  // waits for pending events and folds them into done
+  void reset();
+  ~Prof() { reset(); }
+};
+
+// ---------------------------------------------------------------------------
 // launch bookkeeping
 // ---------------------------------------------------------------------------
 struct Exec {
@@ -92,9 +113,14 @@ struct Exec {
   uint64_t* launches = nullptr;  // incremented for every kernel launch
   int* dev_flag = nullptr;       // device error flag (bounded waits, bad shapes)
   int sm_count = 148;
+  Prof* prof = nullptr;
   void count(uint64_t k = 1) const {
     if (launches) *launches += k;
   }
+  // brackets a launch with events when the timer is on and the launch is tagged
+  bool timing(const char* tag) const { return prof && prof->on && tag; }
+  void mark_begin(cudaEvent_t* a) const;
+  void mark_end(const char* tag, cudaEvent_t a, double flops) const;
 };
 
 // ---------------------------------------------------------------------------
@@ -122,7 +148,7 @@ struct GemmArgs {
 };
 
 // Tensor-core GEMM (gemm_tc.cu): same contract as the FP64 kernel, run on tcgen05.
-void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g);
+void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag = nullptr);
 
 // ---------------------------------------------------------------------------
 // tensors and contractions
@@ -148,7 +174,7 @@ TView view_strided(double* p, const char* labels, std::initializer_list<int> ext
 // are batch modes, labels in A and C the row modes, in B and C the column modes, labels in
 // A and B only are summed. prec selects the FP64 FMA kernel or the tensor-core kernel.
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
-              double beta, const TView& C);
+              double beta, const TView& C, const char* tag = nullptr);
 
 // ---------------------------------------------------------------------------
 // kernels with host launchers (elementwise.cu)

@@ -226,10 +226,10 @@ long long group_size(const std::vector<Mode>& g) {
 
 long long inner_stride(const CIdx& c) { return (c.e1 == 1 && c.e2 == 1) ? c.s0 : c.s2; }
 
-void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g) {
+void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   if (prec != CC_FP64) {
-    gemm_tc(ex, prec, g);
+    gemm_tc(ex, prec, g, tag);
     return;
   }
   const long long tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
@@ -251,6 +251,8 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g) {
   }
   long long zb = std::min<long long>(g.batch, std::max<long long>(1, 65535 / splits));
   dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)(zb * splits));
+  cudaEvent_t ev = nullptr;
+  if (ex.timing(tag)) ex.mark_begin(&ev);
   gemm_f64_kernel<<<grid, NT, 0, ex.stream>>>(g);
   ex.count();
   CC_CUDA(cudaGetLastError());
@@ -261,13 +263,14 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g) {
     ex.count();
     CC_CUDA(cudaGetLastError());
   }
+  if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
   // part returns to the pool here; later launches on the same stream are ordered after the reduce
 }
 
 }  // namespace
 
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
-              double beta, const TView& C) {
+              double beta, const TView& C, const char* tag) {
   auto find = [](const TView& t, char l) {
     for (int d = 0; d < t.nd; ++d)
       if (t.lab[d] == l) return d;
@@ -362,7 +365,7 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
     gi.B = B.p + ob;
     gi.C = C.p + oc;
     if (!first_k) gi.beta = 1.0;
-    launch_gemm(ex, prec, gi);
+    launch_gemm(ex, prec, gi, tag);
     int q = nl - 1;
     while (q >= 0) {
       if (++idx[q] < loops[q].ext) break;

@@ -281,7 +281,7 @@ constexpr size_t SMEM_BYTES = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES 
 
 }  // namespace
 
-void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g) {
+void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
   CC_REQUIRE(prec == CC_MIXED_TF32, CC_ERR_INVALID, "tensor-core precision not available");
   CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
   if (g.K <= 0) {
@@ -323,9 +323,12 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g) {
     attr = true;
   }
   dim3 grid(rowsB / TN, rowsA / TM, g.batch);
+  cudaEvent_t ev = nullptr;
+  if (ex.timing(tag)) ex.mark_begin(&ev);
   gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
   ex.count();
   CC_CUDA(cudaGetLastError());
+  if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
 }
 
 }  // namespace ccpnk
