@@ -144,6 +144,21 @@ int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2,
 int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2,
              int use_guess, cc_report* report);
 
+/* The correlation energy E(t) of cc_residual, computed without allocating any device memory.
+ * The paper has no counterpart: this is a service for callers that cannot call cudaMalloc at
+ * this point (code inside another framework's memory arena, real-time loops that must stay
+ * out of the driver's allocator, processes whose device memory is reserved up front).
+ * t1 (o x v), t2 (o x o x v x v, already satisfying t_ij^ab = t_ji^ba) and energy (one double)
+ * are device pointers on the problem's device; the call enqueues the work on `stream`
+ * (a cudaStream_t, NULL for the default stream) and returns without waiting.
+ * Scratch: up to 1024 partial sums in a fixed device array inside the library (8 KB per GPU
+ * that loads it, held until exit); a launch that would need more partial sums is rejected
+ * with CC_ERR_INVALID. Every call shares that array, so calls that overlap on the GPU (on
+ * different streams, or from different threads) race; order them on one stream. The first
+ * call on a device looks up the array's device address; make that first call before any
+ * stream capture. Returns CC_OK, CC_ERR_INVALID (NULL pointer, bad sizes) or CC_ERR_CUDA. */
+int cc_energy_noalloc(const cc_sys* sys, const double* t1, const double* t2, double* energy, void* stream);
+
 /* Continuous-batching server on one device: submitted solves are admitted while slots and
  * device memory allow, run concurrently on the device, and complete independently. */
 int cc_server_create(cc_server** srv, int device, size_t mem_budget, int max_slots);

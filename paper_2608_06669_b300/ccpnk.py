@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
             "cc_jvp": (i, [vp, vp, vp, vp, vp, vp, vp, vp, i]),
             "cc_apply_AF": (i, [vp, vp, vp, vp, vp, vp, i, i]),
             "cc_solve": (i, [vp, vp, ctypes.POINTER(SolveOpts), vp, vp, i, ctypes.POINTER(Report)]),
+            "cc_energy_noalloc": (i, [vp, vp, vp, vp, vp]),
             "cc_server_create": (i, [pp, i, sz, i]),
             "cc_server_destroy": (None, [vp]),
             "cc_serve_submit": (i, [vp, i, i, i, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(u64)]),

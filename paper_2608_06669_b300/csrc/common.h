@@ -202,6 +202,8 @@ void k_multi_axpy(const Exec& ex, int m, size_t n, const double* Q, size_t ldq, 
 // energy terms: E = sum (2 g_iajb - g_ibja)(t2_ijab + t1_ia t1_jb) + 2 sum f_ia t1_ia
 void k_energy(const Exec& ex, int o, int v, const double* govov, const double* t1, const double* t2,
               const double* fov, int ldf, double* out, double* scratch);
+// number of per-block partial sums (scratch doubles) k_energy uses for an (o, v) problem
+int k_energy_partials(const Exec& ex, int o, int v);
 // scaled elementwise divide: y = x / (D + shift) with D built from diagonal Fock entries
 void k_denom_divide(const Exec& ex, int o, int v, const double* fdiag, double shift,
                     const double* x1, const double* x2, double* y1, double* y2, double scale);

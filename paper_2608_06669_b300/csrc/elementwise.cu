@@ -376,6 +376,7 @@ void k_energy(const Exec& ex, int o, int v, const double* govov, const double* t
   final_reduce_kernel<<<1, TPB, 0, ex.stream>>>(1, nb, scratch, out);
   LAUNCH_CHECK();
 }
+int k_energy_partials(const Exec& ex, int o, int v) { return grid_for(ex, (size_t)o * o * v * v, 4); }
 void k_denom_divide(const Exec& ex, int o, int v, const double* fdiag, double shift, const double* x1,
                     const double* x2, double* y1, double* y2, double scale) {
   size_t n = (size_t)o * v + (size_t)o * o * v * v;
