@@ -5,9 +5,10 @@ One step is one complete preconditioned Newton-Krylov solve (every step of the h
 T1 dressing, intermediates, the particle-particle ladder, hole ladder and rings, the
 singles, the energy, the analytic JVP, A_F and its inner GMRES, the outer CGS2 Arnoldi
 with Eisenstat-Walker forcing and the Newton update) from the generalised-MP2 start to
-||R|| < 1e-8, in the mixed path (TF32 tensor-core JVPs and inner solves, FP64 outer
-residual). Inputs are resident on the device before the timed region; L2 is flushed
-between steps. The line also carries the FP64 PNK time, the roofline of the dominant
+||R|| < 1e-8, in the mixed path (JVPs on tcgen05 with the three-pass TF32 split, FP64
+outer residual, energy, update and orthogonalisation; A_F^{-1} applied exactly in the Fock
+eigenbasis, the paper's inner-GMRES inversion timed beside it). Inputs are resident on the
+device before the timed region; L2 is flushed between steps. The line also carries the FP64 PNK time, the roofline of the dominant
 kernel, the CPU oracle baseline and an end-to-end time through the C ABI with host buffers.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -181,7 +182,8 @@ def run_ours(args):
     g = ccpnk.System.from_synth(ctx, s)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
-    kw = dict(method="pnk", prec=args.prec)
+    # A_F^{-1} exactly in the Fock eigenbasis; the paper's inner-GMRES inversion is timed beside it
+    kw = dict(method="pnk", prec=args.prec, af_direct=0 if args.af_gmres else 1)
 
     for _ in range(args.warmup):
         g.solve(**kw)
@@ -215,8 +217,12 @@ def run_ours(args):
 
     # FP64 PNK on the same workload (the mixed path must beat it)
     t0 = time.perf_counter()
-    _, _, rep64 = g.solve(method="pnk", prec="fp64")
+    _, _, rep64 = g.solve(method="pnk", prec="fp64", af_direct=kw["af_direct"])
     t_fp64 = time.perf_counter() - t0
+    # the same mixed solve with A_F inverted by inner GMRES (the paper's protocol)
+    t0 = time.perf_counter()
+    _, _, rep_gm = g.solve(method="pnk", prec=args.prec, af_direct=0)
+    t_gmres = time.perf_counter() - t0
 
     # end to end through the C ABI with host buffers: upload the problem, solve, read back
     n = s.o + s.v
@@ -254,9 +260,10 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "tf32+f64", "data": "synthetic",
+        "dtype": {"tf32x3": "tf32x3+f64", "tf32": "tf32+f64", "fp64": "f64"}[args.prec], "data": "synthetic",
         "config": {"workload": WORKLOAD, "o": s.o, "v": s.v, "naux": s.naux, "gauge": "rotated (off-diagonal f up to 0.1 Eh)",
                    "method": "pnk", "prec": args.prec, "tol": 1e-8, "start": "generalised MP2",
+                   "af_inverse": "gmres" if args.af_gmres else "eigenbasis",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof, "roofline_tensor": roof_tc,
         "cpu_baseline": cpu,
@@ -265,6 +272,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "fp64_pnk_s": t_fp64,
         "speedup_mixed_vs_fp64": t_fp64 / t_max,
+        "mixed_pnk_af_gmres_s": t_gmres,
+        "solve_af_gmres": {k: rep_gm[k] for k in ("energy", "res_norm", "newton_iters", "jvps", "af_applies")},
         "solve": {k: reports[-1][k] for k in ("energy", "res_norm", "newton_iters", "residual_evals", "jvps",
                                                "af_applies", "krylov_iters")},
         "solve_fp64": {k: rep64[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
@@ -281,7 +290,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32", choices=["tf32", "fp64"])
+    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "tf32", "fp64"])
+    ap.add_argument("--af-gmres", action="store_true", help="invert A_F by inner GMRES in the timed solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
     if args.impl == "reference":

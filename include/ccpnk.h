@@ -51,7 +51,9 @@ extern "C" {
 typedef enum {
   CC_FP64 = 0,          /* every contraction in FP64 (FMA pipe) */
   CC_MIXED_TF32 = 1,    /* contractions of JVPs / inner solves on tcgen05 TF32, FP32 accumulate */
-  CC_MIXED_BF16X3 = 2   /* reserved: 3-pass BF16-split contractions (returns CC_ERR_INVALID today) */
+  CC_MIXED_BF16X3 = 2,  /* reserved: 3-pass BF16-split contractions (returns CC_ERR_INVALID today) */
+  CC_MIXED_TF32X3 = 3   /* 3-pass TF32 split: x = hi + lo, a b ~ hi hi + hi lo + lo hi on tcgen05,
+                           FP32 accumulate (about FP32 accuracy at a third of the TF32 rate) */
 } cc_precision;
 
 typedef enum {
@@ -77,7 +79,7 @@ typedef struct {
   double level_shift;    /* FP+DIIS denominator shift, App. D (default 0) */
   int diis_size;         /* FP+DIIS subspace size (default 8; 0 disables DIIS) */
   int jvp_fd;            /* 1: forward finite-difference JVP (Eq. jacobian_vector_product_via_finite_difference) */
-  double inner_rtol;     /* inner A_F GMRES relative tolerance (default 1e-12 FP64 / 1e-6 mixed) */
+  double inner_rtol;     /* inner A_F GMRES relative tolerance (default 1e-12 FP64, 1e-8 TF32X3, 1e-6 TF32) */
   int inner_max;         /* inner GMRES cap (default 50) */
   int af_direct;         /* 1: invert A_F in the Fock eigenbasis instead of by inner GMRES */
   int verbose;           /* 1: one line per outer iteration on stderr */

@@ -44,18 +44,28 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// out[b][r][k] for r < rows_pad, k < k_pad (FP32, TF32-rounded), zero outside rows x K
+// out[b][r][s * k_pad + k] for r < rows_pad, k < k_pad and the nseg segments s of a row
+// (FP32, TF32-rounded, zero outside rows x K). seg_lo is a bit mask of the segments that hold
+// the low part lo = tf32(x - hi) instead of the high part hi = tf32(x); one segment with
+// mask 0 is the plain TF32 operand, three segments [hi|hi|lo] and [hi|lo|hi] on the two
+// operands give the three-pass split product hi hi + hi lo + lo hi along one long k.
 __global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
-                              int batch, int rows_pad, int k_pad, float* __restrict__ out) {
+                              int batch, int rows_pad, int k_pad, int nseg, int seg_lo, float* __restrict__ out) {
   const size_t tot = (size_t)batch * rows_pad * k_pad;
+  const size_t row_len = (size_t)nseg * k_pad;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     int k = (int)(e % k_pad);
     size_t q = e / k_pad;
     int r = (int)(q % rows_pad);
     int b = (int)(q / rows_pad);
-    float v = 0.0f;
-    if (r < rows && k < K) v = to_tf32((float)src[cidx(bix, b) + cidx(rix, r) + cidx(kix, k)]);
-    out[e] = v;
+    float hi = 0.0f, lo = 0.0f;
+    if (r < rows && k < K) {
+      double x = src[cidx(bix, b) + cidx(rix, r) + cidx(kix, k)];
+      hi = to_tf32((float)x);
+      lo = to_tf32((float)(x - (double)hi));
+    }
+    float* row = out + q * row_len + k;
+    for (int s = 0; s < nseg; ++s) row[(size_t)s * k_pad] = ((seg_lo >> s) & 1) ? lo : hi;
   }
 }
 
@@ -210,8 +220,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective: decide per warp
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    const long long crow = row < g.M ? cidx(g.cb, bz) + cidx(g.cm, row) : 0;
+    // each warp turns its 32 x 32 chunk around in shared memory (the pipeline buffers are
+    // idle once every MMA has completed) so that a warp's stores run along a row of C
+    float* tile = reinterpret_cast<float*>(sA) + warp * (32 * 33);
+    const long long cbase = cidx(g.cb, bz);
 #pragma unroll 1
     for (int c0 = 0; c0 < TN; c0 += 32) {
       uint32_t r[32];
@@ -225,18 +237,22 @@ __global__ void __launch_bounds__(THREADS, 1)
             "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < g.M) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < g.N) {
-            double* c = g.C + crow + cidx(g.cn, n);
-            double val = g.alpha * (double)__uint_as_float(r[j]);
-            if (g.beta != 0.0) val = fma(g.beta, *c, val);
-            *c = val;
-          }
+      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+      __syncwarp();
+      const int n = n0 + c0 + lane;
+      const long long cn = n < g.N ? cidx(g.cn, n) : 0;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const int row = m0 + warp * 32 + rr;
+        if (row < g.M && n < g.N) {
+          double* c = g.C + cbase + cidx(g.cm, row) + cn;
+          double val = g.alpha * (double)tile[rr * 33 + lane];
+          if (g.beta != 0.0) val = fma(g.beta, *c, val);
+          *c = val;
         }
       }
+      __syncwarp();
     }
   }
   if (warp == 0 && lane == 0) {
@@ -282,7 +298,7 @@ constexpr size_t SMEM_BYTES = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES 
 }  // namespace
 
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
-  CC_REQUIRE(prec == CC_MIXED_TF32, CC_ERR_INVALID, "tensor-core precision not available");
+  CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3, CC_ERR_INVALID, "tensor-core precision not available");
   CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
   if (g.K <= 0) {
     int blocks = (int)std::min<size_t>(((size_t)g.batch * g.M * g.N + 255) / 256, (size_t)ex.sm_count * 8);
@@ -294,22 +310,28 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   CC_REQUIRE(g.batch <= 65535, CC_ERR_INVALID, "tensor-core contraction: batch too large");
   const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
   const int k_pad = (g.K + TK - 1) / TK * TK;
-  const size_t nA = (size_t)g.batch * rowsA * k_pad, nB = (size_t)g.batch * rowsB * k_pad;
+  // the split precision stages [hi|hi|lo] against [hi|lo|hi] along a three times longer k
+  const int nseg = prec == CC_MIXED_TF32X3 ? 3 : 1;
+  const int kk = nseg * k_pad;
+  const size_t nA = (size_t)g.batch * rowsA * kk, nB = (size_t)g.batch * rowsB * kk;
   DBuf<double> stA(ex.pool, (nA + 1) / 2), stB(ex.pool, (nB + 1) / 2);
   float* fA = reinterpret_cast<float*>(stA.p);
   float* fB = reinterpret_cast<float*>(stB.p);
+  const size_t eA = (size_t)g.batch * rowsA * k_pad, eB = (size_t)g.batch * rowsB * k_pad;
   auto blocks_for = [&](size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)ex.sm_count * 16)); };
-  gather_kernel<<<blocks_for(nA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, fA);
+  gather_kernel<<<blocks_for(eA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, nseg,
+                                                        nseg == 3 ? 0b100 : 0, fA);
   ex.count();
-  gather_kernel<<<blocks_for(nB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad, fB);
+  gather_kernel<<<blocks_for(eB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad, nseg,
+                                                        nseg == 3 ? 0b010 : 0, fB);
   ex.count();
   CC_CUDA(cudaGetLastError());
-  CUtensorMap mA = make_map(fA, k_pad, rowsA, g.batch, TM);
-  CUtensorMap mB = make_map(fB, k_pad, rowsB, g.batch, TN);
+  CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM);
+  CUtensorMap mB = make_map(fB, kk, rowsB, g.batch, TN);
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
-  a.kblocks = k_pad / TK;
+  a.kblocks = kk / TK;
   a.cm = g.cm;
   a.cn = g.cn;
   a.cb = g.cb;

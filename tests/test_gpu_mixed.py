@@ -66,6 +66,24 @@ def test_tf32_residual_and_jvp(ctx, o, v, naux, gauge):
     assert np.abs(j2 - p2).max() < TF32_TOL * scale and np.abs(j1 - p1).max() < TF32_TOL * scale
 
 
+@pytest.mark.parametrize("o,v,naux,gauge", [(2, 4, 5, "haar"), (7, 33, 20, "haar")])
+def test_tf32x3_residual_and_jvp(ctx, o, v, naux, gauge):
+    """The three-pass split keeps about FP32 accuracy: 1e-6 normwise."""
+    s = synth.make_system(o, v, naux, seed=9 + o, gauge=gauge)
+    rng = np.random.default_rng(o + 3 * v)
+    t1, t2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    d1, d2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    g = gsys(ctx, s)
+    r1, r2, _ = g.residual(t1, t2, prec="tf32x3")
+    q1, q2, _ = cc.residual(s.fock, s.B, o, t1, t2)
+    scale = max(np.abs(q1).max(), np.abs(q2).max())
+    assert np.abs(r2 - q2).max() < 1e-6 * scale and np.abs(r1 - q1).max() < 1e-6 * scale
+    j1, j2 = g.jvp(t1, t2, d1, d2, prec="tf32x3")
+    p1, p2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+    scale = max(np.abs(p1).max(), np.abs(p2).max())
+    assert np.abs(j2 - p2).max() < 1e-6 * scale and np.abs(j1 - p1).max() < 1e-6 * scale
+
+
 def test_tf32_jvp_workload_error(ctx):
     """The error of the TF32 JVP on the o=10, v=90 workload, stated against the FP64 oracle."""
     s = synth.workload("o10v90_rotated")
@@ -78,11 +96,11 @@ def test_tf32_jvp_workload_error(ctx):
     assert err < TF32_TOL
 
 
-@pytest.mark.parametrize("method", ["pnk", "nk"])
-def test_mixed_solve_reaches_fp64_root(ctx, method):
+@pytest.mark.parametrize("method,prec", [("pnk", "tf32"), ("nk", "tf32"), ("pnk", "tf32x3")])
+def test_mixed_solve_reaches_fp64_root(ctx, method, prec):
     s = synth.workload("o5v20_canonical")
     ref = json.load(open(GOLDEN))["o5v20_canonical"]["e_corr"]
-    _, _, rep = gsys(ctx, s).solve(method, "tf32")
+    _, _, rep = gsys(ctx, s).solve(method, prec)
     assert rep["status_code"] == 0, rep
     assert rep["res_norm"] < 1e-8 and abs(rep["energy"] - ref) < 1e-8
 
