@@ -284,8 +284,62 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """The served mix: requests of uneven (o, v) (o ~ U{4..16}, v = round(o U[6,9]),
+    naux = 3(o+v), half canonical, half Haar-rotated) arriving with exponential gaps
+    (mean 20 ms), submitted to the continuous-batching server at their arrival times;
+    reports solves/s and p50/p99 time-to-solution for the mixed path and the FP64 path."""
+    import numpy as np
+
+    from paper_2608_06669_b300 import ccpnk, synth
+
+    reqs_all = synth.served_requests(args.serve)
+    out = {}
+    # the FP64 path is ~4-12x slower per solve, so it serves the first requests of the same
+    # stream only (the mixed path serves all of them); both cap a solve at max_newton steps
+    for prec, reqs in (("tf32x3", reqs_all), ("fp64", reqs_all[: args.serve_fp64])):
+        srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=args.slots)
+        t_start = time.perf_counter()
+        tickets = []
+        for arrival, s in reqs:
+            wait = arrival - (time.perf_counter() - t_start)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(srv.submit(s.o, s.v, s.naux, s.fock, s.B, "pnk", prec, af_direct=1,
+                                      max_outer=args.max_newton))
+        results = {}
+        while len(results) < len(tickets):
+            for t in tickets:
+                if t not in results:
+                    r = srv.poll(t)
+                    if r is not None:
+                        results[t] = r
+            time.sleep(0.005)
+        times = [srv.times(t) for t in tickets]
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([f - sub for sub, _, f in times])
+        span = max(f for _, _, f in times) - min(sub for sub, _, _ in times)
+        conv = [results[t][2]["status_code"] == 0 for t in tickets]
+        out[prec] = {"solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
+                     "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(conv)), "requests": len(tickets),
+                     "max_concurrent": stats["max_running"], "makespan_s": span,
+                     "not_converged": [f"o{s.o}v{s.v}" for (_, s), c in zip(reqs, conv) if not c]}
+    line = {"metric": METRIC, "mode": "served", "value": out["tf32x3"]["p99_s"], "unit": "s (p99 time-to-solution)",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "tf32x3+f64", "data": "synthetic",
+            "config": {"workload": "served mix", "requests": args.serve, "arrivals": "exponential, mean 20 ms",
+                       "o": "U{4..16}", "v": "round(o U[6,9])", "naux": "3(o+v)", "gauges": "canonical / Haar",
+                       "slots": args.slots, "af_inverse": "eigenbasis"},
+            "mixed": out["tf32x3"], "fp64": out["fp64"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests instead")
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-fp64", type=int, default=8, help="requests the FP64 pass of --serve runs")
+    ap.add_argument("--max-newton", type=int, default=30, help="Newton-step cap of a served solve")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -296,6 +350,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

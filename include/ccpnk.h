@@ -161,18 +161,27 @@ int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, do
  * stream capture. Returns CC_OK, CC_ERR_INVALID (NULL pointer, bad sizes) or CC_ERR_CUDA. */
 int cc_energy_noalloc(const cc_sys* sys, const double* t1, const double* t2, double* energy, void* stream);
 
-/* Continuous-batching server on one device: submitted solves are admitted while slots and
- * device memory allow, run concurrently on the device, and complete independently. */
+/* Continuous-batching server on one device (the serving pattern of the solver; the paper
+ * solves one problem at a time). max_slots worker slots, each with its own stream and memory
+ * pool, take submitted solves in arrival order as soon as a slot is free and the request's
+ * device-memory estimate fits under mem_budget (0: no budget), so the kernels of different
+ * requests overlap on the device. Results are bitwise independent of what else runs. */
 int cc_server_create(cc_server** srv, int device, size_t mem_budget, int max_slots);
+/* Finishes the running solves, drops queued ones and frees everything. */
 void cc_server_destroy(cc_server* srv);
-/* Copies the problem (host pointers) before returning; ticket identifies the request. */
+/* Copies the problem (host pointers) before returning; ticket identifies the request.
+ * CC_ERR_OOM if the request's estimate exceeds the whole budget (it could never run). */
 int cc_serve_submit(cc_server* srv, int o, int v, int naux, const double* fock, const double* B,
                     const cc_solve_opts* opts, uint64_t* ticket);
-/* CC_PENDING while the request runs; then its cc_solve status, with report filled and the
- * solution copied to t1/t2 (host, may be NULL). A finished ticket is released by this call. */
+/* CC_PENDING while the request waits or runs; then its cc_solve status, with report filled and
+ * the solution copied to t1/t2 (host, may be NULL). That call releases the amplitudes; the
+ * ticket's times stay available through cc_serve_times. */
 int cc_serve_poll(cc_server* srv, uint64_t ticket, cc_report* report, double* t1, double* t2);
-/* Timestamps of a finished request (seconds since server creation): submit, admit, finish. */
+/* Timestamps of a request in seconds since server creation: submit, admit, finish (CC_PENDING
+ * until it has finished). */
 int cc_serve_times(cc_server* srv, uint64_t ticket, double* t_submit, double* t_admit, double* t_finish);
+/* Requests running now, waiting now, the most that ran at once, and admitted bytes. */
+int cc_server_stats(cc_server* srv, int* running, int* queued, int* max_running, size_t* bytes_admitted);
 
 #ifdef __cplusplus
 }

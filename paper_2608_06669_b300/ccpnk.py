@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
             "cc_serve_submit": (i, [vp, i, i, i, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(u64)]),
             "cc_serve_poll": (i, [vp, u64, ctypes.POINTER(Report), vp, vp]),
             "cc_serve_times": (i, [vp, u64, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
+            "cc_server_stats": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -257,6 +258,65 @@ class System:
         d = rep.as_dict()
         d["status_code"] = st
         return o1, o2, d
+
+
+class Server:
+    """The continuous-batching server (cc_server): submit() returns a ticket at once; poll()
+    returns None while the request waits or runs, then (t1, t2, report dict)."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0, max_slots: int = 4):
+        h = ctypes.c_void_p()
+        st = lib().cc_server_create(ctypes.byref(h), device, mem_budget, max_slots)
+        if st < 0:
+            raise CCError(st, "cc_server_create failed")
+        self.h = h
+        self.shapes = {}
+
+    def submit(self, o, v, naux, fock, B, method="pnk", prec="fp64", **kw) -> int:
+        keep = []
+        opts = default_opts(method, prec, **kw)
+        t = ctypes.c_uint64()
+        st = lib().cc_serve_submit(self.h, o, v, naux, _ptr(np.asarray(fock), keep), _ptr(np.asarray(B), keep),
+                                   ctypes.byref(opts), ctypes.byref(t))
+        if st < 0:
+            raise CCError(st, "cc_serve_submit failed")
+        self.shapes[t.value] = (o, v)
+        return t.value
+
+    def poll(self, ticket: int):
+        o, v = self.shapes[ticket]
+        t1 = np.empty((o, v))
+        t2 = np.empty((o, o, v, v))
+        rep = Report()
+        st = lib().cc_serve_poll(self.h, ticket, ctypes.byref(rep), ctypes.c_void_p(t1.ctypes.data),
+                                 ctypes.c_void_p(t2.ctypes.data))
+        if st == CC_PENDING:
+            return None
+        d = rep.as_dict()
+        d["status_code"] = st
+        return t1, t2, d
+
+    def times(self, ticket: int):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        lib().cc_serve_times(self.h, ticket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return a.value, b.value, c.value
+
+    def stats(self):
+        r, q, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        b = ctypes.c_size_t()
+        lib().cc_server_stats(self.h, ctypes.byref(r), ctypes.byref(q), ctypes.byref(m), ctypes.byref(b))
+        return {"running": r.value, "queued": q.value, "max_running": m.value, "bytes_admitted": b.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def default_opts(method="pnk", prec="fp64", **kw) -> SolveOpts:

@@ -1,10 +1,235 @@
-// Continuous-batching server (placeholder until the scheduler lands).
-#include "common.h"
+// Continuous-batching server: CC solves submitted at any time are admitted as soon as a
+// slot and device memory are free, run concurrently on the device (one stream and one
+// memory pool per slot, so kernels of different requests overlap), and complete
+// independently. Every kernel is deterministic, so a request's result does not depend on
+// what else runs.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "handles.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  int o = 0, v = 0, naux = 0;
+  std::vector<double> fock, B;  // host copies taken at submit
+  cc_solve_opts opts{};
+  size_t footprint = 0;  // admission estimate (bytes)
+  // results
+  bool done = false, released = false;
+  int status = CC_PENDING;
+  cc_report report{};
+  std::vector<double> t1, t2;
+  double t_submit = 0, t_admit = 0, t_finish = 0;
+  std::string err;
+};
+
+// Device bytes a solve is expected to hold: the resident problem, the engine's intermediates
+// and tangents, the ladder slab, the Krylov bases (outer and inner) and the tensor-core staging.
+size_t footprint_bytes(int o, int v, int naux, const cc_solve_opts& op) {
+  const double n = o + v, ov = (double)o * v, oovv = ov * ov;
+  const double namp = ov + oovv;
+  const double per_a = 8.0 * (double)v * v * v;
+  const double lb = std::max(1.0, std::min((double)v, 512.0 * 1024 * 1024 / std::max(per_a, 1.0)));
+  double doubles = 0;
+  doubles += 3.0 * naux * n * n;                            // B (upload, blocks)
+  doubles += 36.0 * oovv + 8.0 * naux * n * n;              // engine values + tangents
+  doubles += lb * v * v * v;                                // ladder slab
+  doubles += (op.m_max + 8.0) * namp;                       // outer Krylov basis and vectors
+  doubles += (op.af_direct ? 2.0 : (op.inner_max + 2.0)) * namp;  // A_F inverse work
+  doubles += 4.0 * oovv;                                    // split-k partials, staging
+  return (size_t)(doubles * 8.0 * 1.15) + (64u << 20);
+}
+
+}  // namespace
+
+struct cc_server {
+  int device = 0;
+  size_t budget = 0;  // 0: no limit
+  int max_slots = 1;
+  Clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> queue;
+  std::map<uint64_t, std::unique_ptr<Request>> all;
+  uint64_t next_ticket = 1;
+  size_t in_use = 0;
+  int running = 0, max_running = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+void worker_main(cc_server* srv, int slot) {
+  (void)slot;
+  cudaSetDevice(srv->device);
+  cc_ctx* ctx = nullptr;
+  int st = cc_ctx_create(&ctx, srv->device, 0, nullptr);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      // FIFO admission: the oldest request goes first once its memory estimate fits
+      srv->cv.wait(lk, [&] {
+        if (srv->stop) return true;
+        if (srv->queue.empty()) return false;
+        Request* h = srv->queue.front();
+        return srv->budget == 0 || srv->in_use + h->footprint <= srv->budget || srv->running == 0;
+      });
+      if (srv->stop) break;
+      r = srv->queue.front();
+      srv->queue.pop_front();
+      srv->in_use += r->footprint;
+      srv->running += 1;
+      srv->max_running = std::max(srv->max_running, srv->running);
+      r->t_admit = srv->now();
+    }
+    int status = CC_ERR_CUDA;
+    std::string err;
+    cc_report rep{};
+    std::vector<double> t1((size_t)r->o * r->v), t2((size_t)r->o * r->o * r->v * r->v);
+    if (st == CC_OK && ctx) {
+      cc_sys* sys = nullptr;
+      status = cc_sys_create(ctx, r->o, r->v, r->naux, r->fock.data(), r->B.data(), &sys);
+      if (status == CC_OK) {
+        status = cc_solve(ctx, sys, &r->opts, t1.data(), t2.data(), 0, &rep);
+        cc_sys_destroy(sys);
+      }
+      if (status < 0 && status != CC_ERR_NOT_CONVERGED && status != CC_ERR_DIVERGED) err = cc_last_error(ctx);
+    } else {
+      err = "no device context for this slot";
+    }
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      r->status = status;
+      r->report = rep;
+      r->t1.swap(t1);
+      r->t2.swap(t2);
+      r->err = err;
+      r->t_finish = srv->now();
+      r->done = true;
+      r->fock.clear();
+      r->fock.shrink_to_fit();
+      r->B.clear();
+      r->B.shrink_to_fit();
+      srv->in_use -= r->footprint;
+      srv->running -= 1;
+    }
+    srv->cv.notify_all();
+  }
+  if (ctx) cc_ctx_destroy(ctx);
+}
+
+}  // namespace
 
 extern "C" {
-int cc_server_create(cc_server** srv, int, size_t, int) { if (srv) *srv = nullptr; return CC_ERR_INVALID; }
-void cc_server_destroy(cc_server*) {}
-int cc_serve_submit(cc_server*, int, int, int, const double*, const double*, const cc_solve_opts*, uint64_t*) { return CC_ERR_INVALID; }
-int cc_serve_poll(cc_server*, uint64_t, cc_report*, double*, double*) { return CC_ERR_INVALID; }
-int cc_serve_times(cc_server*, uint64_t, double*, double*, double*) { return CC_ERR_INVALID; }
+
+int cc_server_create(cc_server** out, int device, size_t mem_budget, int max_slots) {
+  if (!out || max_slots < 1) return CC_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return CC_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return CC_ERR_INVALID;
+  std::unique_ptr<cc_server> s(new cc_server);
+  s->device = device;
+  s->budget = mem_budget;
+  s->max_slots = max_slots;
+  s->t0 = Clock::now();
+  for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker_main, s.get(), i);
+  *out = s.release();
+  return CC_OK;
 }
+
+void cc_server_destroy(cc_server* srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv.notify_all();
+  for (auto& w : srv->workers) w.join();
+  delete srv;
+}
+
+int cc_serve_submit(cc_server* srv, int o, int v, int naux, const double* fock, const double* B,
+                    const cc_solve_opts* opts, uint64_t* ticket) {
+  if (!srv || !fock || !B || !opts || !ticket || o < 1 || v < 1 || naux < 1) return CC_ERR_INVALID;
+  std::unique_ptr<Request> r(new Request);
+  const size_t n = (size_t)o + v;
+  r->o = o;
+  r->v = v;
+  r->naux = naux;
+  r->fock.assign(fock, fock + n * n);
+  r->B.assign(B, B + (size_t)naux * n * n);
+  r->opts = *opts;
+  r->footprint = footprint_bytes(o, v, naux, *opts);
+  if (srv->budget && r->footprint > srv->budget) return CC_ERR_OOM;  // never admissible
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    r->ticket = srv->next_ticket++;
+    r->t_submit = srv->now();
+    *ticket = r->ticket;
+    srv->queue.push_back(r.get());
+    srv->all[r->ticket] = std::move(r);
+  }
+  srv->cv.notify_all();
+  return CC_OK;
+}
+
+int cc_serve_poll(cc_server* srv, uint64_t ticket, cc_report* report, double* t1, double* t2) {
+  if (!srv) return CC_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->all.find(ticket);
+  if (it == srv->all.end() || it->second->released) return CC_ERR_INVALID;
+  Request* r = it->second.get();
+  if (!r->done) return CC_PENDING;
+  if (report) *report = r->report;
+  if (t1) memcpy(t1, r->t1.data(), r->t1.size() * sizeof(double));
+  if (t2) memcpy(t2, r->t2.data(), r->t2.size() * sizeof(double));
+  r->released = true;
+  r->t1.clear();
+  r->t1.shrink_to_fit();
+  r->t2.clear();
+  r->t2.shrink_to_fit();
+  return r->status;
+}
+
+int cc_serve_times(cc_server* srv, uint64_t ticket, double* t_submit, double* t_admit, double* t_finish) {
+  if (!srv) return CC_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->all.find(ticket);
+  if (it == srv->all.end()) return CC_ERR_INVALID;
+  Request* r = it->second.get();
+  if (t_submit) *t_submit = r->t_submit;
+  if (t_admit) *t_admit = r->t_admit;
+  if (t_finish) *t_finish = r->t_finish;
+  return r->done ? CC_OK : CC_PENDING;
+}
+
+int cc_server_stats(cc_server* srv, int* running, int* queued, int* max_running, size_t* bytes_admitted) {
+  if (!srv) return CC_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (running) *running = srv->running;
+  if (queued) *queued = (int)srv->queue.size();
+  if (max_running) *max_running = srv->max_running;
+  if (bytes_admitted) *bytes_admitted = srv->in_use;
+  return CC_OK;
+}
+
+}  // extern "C"
