@@ -19,14 +19,14 @@ namespace ccpnk {
 namespace {
 
 constexpr int TM = 128;         // tile rows = UMMA M
-constexpr int TN = 128;         // tile columns = UMMA N
+constexpr int TN = 256;         // tile columns = UMMA N
 constexpr int TK = 32;          // k per pipeline stage: 32 FP32 = one 128-byte swizzle row
 constexpr int UK = 8;           // k per tcgen05.mma of kind::tf32
 constexpr int STAGES = 4;
-constexpr int THREADS = 128;    // four warps: TMA producer, MMA issuer, all four in the epilogue
+constexpr int THREADS = 192;    // six warps: TMA producer, MMA issuer, four epilogue warps
 constexpr uint32_t A_BYTES = TM * TK * 4;
 constexpr uint32_t B_BYTES = TN * TK * 4;
-constexpr uint32_t TMEM_COLS = TN;  // FP32 accumulator columns
+constexpr uint32_t TMEM_COLS = 2 * TN;  // two FP32 accumulators of TN columns (all 512)
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s bound on any wait
 
 __device__ __forceinline__ long long cidx(const CIdx& c, int x) {
@@ -69,6 +69,21 @@ __global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix
   }
 }
 
+// split-k: C = alpha * sum_s part[s] + beta * C, the splits added in a fixed order
+__global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int splits) {
+  const size_t tot = (size_t)g.batch * g.M * g.N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    int n = (int)(e % g.N);
+    size_t r = e / g.N;
+    int m = (int)(r % g.M);
+    int b = (int)(r / g.M);
+    double s = 0.0;
+    for (int q = 0; q < splits; ++q) s += (double)part[(size_t)q * tot + e];
+    double* c = g.C + cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
+    *c = g.beta == 0.0 ? g.alpha * s : fma(g.beta, *c, g.alpha * s);
+  }
+}
+
 __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
   const size_t tot = (size_t)g.batch * g.M * g.N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
@@ -82,10 +97,13 @@ __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
 }
 
 struct TcArgs {
-  int M, N, kblocks;
+  int M, N, kblocks, num_m, num_n, tiles;  // tiles counts splits x batch x num_m x num_n
+  int splits, kchunk;                     // split-k: k blocks [s * kchunk, (s + 1) * kchunk)
+  int batch;
   CIdx cm, cn, cb;
   double alpha, beta;
   double* C;
+  float* part;  // split-k partial sums [splits][batch][M][N] (splits > 1)
   int* err;
 };
 
@@ -107,6 +125,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // waits for the phase of the given parity to complete; false after WAIT_NS
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   unsigned long long t0 = 0;
@@ -118,6 +140,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (it >= 32) __nanosleep(64);  // back off so idle roles do not take issue slots
     if ((it & 63) == 0) {
       unsigned long long t = gtime();
       if (t0 == 0) t0 = t;
@@ -147,28 +170,55 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 // instruction descriptor: D = F32, A = B = TF32, both K-major, N = TN, M = TM
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
+// tile t -> (split, batch entry, first row, first column, k-block range)
+__device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int& bz, int& m0, int& n0, int& kb0,
+                                            int& kb1) {
+  const int per = g.num_m * g.num_n;
+  const int outer = t / per;
+  sp = outer / g.batch;
+  bz = outer - sp * g.batch;
+  const int r = t - outer * per;
+  m0 = (r / g.num_n) * TM;
+  n0 = (r % g.num_n) * TN;
+  kb0 = sp * g.kchunk;
+  kb1 = min(g.kblocks, kb0 + g.kchunk);
+}
+
+// shared memory: STAGES x (A tile, B tile), the epilogue's turn-around tiles, barriers
+constexpr uint32_t EP_FLOATS = 32 * 33;
+constexpr size_t SMEM_USED = (size_t)STAGES * (A_BYTES + B_BYTES) + 4 * EP_FLOATS * 4 + (2 * STAGES + 4) * 8 + 16;
+constexpr size_t SMEM_BYTES = 1024 + SMEM_USED;
+
+// Persistent, warp-specialised GEMM: each CTA walks tiles blockIdx.x, +gridDim.x, ...
+//   warp 0: TMA producer through the STAGES-deep full/empty ring
+//   warp 1: TMEM allocator and the single MMA-issuing thread; alternates two accumulators
+//   warps 2-5: epilogue (TMEM lane quadrant = warp % 4), releasing an accumulator as soon as
+//              it has been read, so the next tile's MMAs overlap this tile's stores
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = (uint64_t*)(sB + STAGES * B_BYTES);  // full[STAGES], empty[STAGES], done
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  float* ep = reinterpret_cast<float*>(sB + STAGES * B_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ep + 4 * EP_FLOATS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN, bz = blockIdx.z;
-
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(TMEM_COLS)
                  : "memory");
@@ -180,90 +230,138 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
 
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kb = 0; kb < g.kblocks; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(empty0 + 8 * s, ph ^ 1)) { ok = false; break; }
-      mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
-      tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, kb * TK, m0, bz);
-      tma_load_3d(smem_u32(sB + s * B_BYTES), &tmB, full0 + 8 * s, kb * TK, n0, bz);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    for (int kb = 0; kb < g.kblocks; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(full0 + 8 * s, ph)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
-#pragma unroll
-      for (int j = 0; j < TK / UK; ++j) {
-        const uint64_t da = sdesc(a0 + j * UK * 4), db = sdesc(b0 + j * UK * 4);
-        const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(IDESC), "r"(acc)
-            : "memory");
-      }
-      // frees the stage once these MMAs have read it
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
-                   : "memory");
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done) : "memory");
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
-  if (!mbar_wait(done, 0)) ok = false;
-  ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective: decide per warp
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    // each warp turns its 32 x 32 chunk around in shared memory (the pipeline buffers are
-    // idle once every MMA has completed) so that a warp's stores run along a row of C
-    float* tile = reinterpret_cast<float*>(sA) + warp * (32 * 33);
-    const long long cbase = cidx(g.cb, bz);
-#pragma unroll 1
-    for (int c0 = 0; c0 < TN; c0 += 32) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%"
-          "22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-            "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-            "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-            "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
-      __syncwarp();
-      const int n = n0 + c0 + lane;
-      const long long cn = n < g.N ? cidx(g.cn, n) : 0;
-#pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        const int row = m0 + warp * 32 + rr;
-        if (row < g.M && n < g.N) {
-          double* c = g.C + cbase + cidx(g.cm, row) + cn;
-          double val = g.alpha * (double)tile[rr * 33 + lane];
-          if (g.beta != 0.0) val = fma(g.beta, *c, val);
-          *c = val;
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t q = 0;  // pipeline slot counter, continued across tiles
+      for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+        int sp, bz, m0, n0, kb0, kb1;
+        tile_coords(g, t, sp, bz, m0, n0, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb, ++q) {
+          const int s = q % STAGES;
+          const uint32_t ph = (q / STAGES) & 1;
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1)) { ok = false; break; }
+          mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
+          tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, kb * TK, m0, bz);
+          tma_load_3d(smem_u32(sB + s * B_BYTES), &tmB, full0 + 8 * s, kb * TK, n0, bz);
         }
       }
-      __syncwarp();
+      // never leave with copies in flight: the last loads issued must have landed (bounded)
+      for (uint32_t r = q > (uint32_t)STAGES ? q - STAGES : 0; r < q; ++r)
+        if (!mbar_wait(full0 + 8 * (r % STAGES), (r / STAGES) & 1)) ok = false;
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t q = 0;
+      int it = 0;
+      for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(acc * TN);
+        int sp, bz, m0, n0, kb0, kb1;
+        tile_coords(g, t, sp, bz, m0, n0, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb, ++q) {
+          const int s = q % STAGES;
+          const uint32_t ph = (q / STAGES) & 1;
+          if (!mbar_wait(full0 + 8 * s, ph)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+          for (int j = 0; j < TK / UK; ++j) {
+            const uint64_t da = sdesc(a0 + j * UK * 4), db = sdesc(b0 + j * UK * 4);
+            const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(da), "l"(db), "r"(IDESC), "r"(accum)
+                : "memory");
+          }
+          // frees the stage once these MMAs have read it
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                       : "memory");
+        }
+        if (!ok) break;
+        // the accumulator is complete once every MMA issued so far has finished
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tfull0 + 8 * acc)
+                     : "memory");
+      }
+    }
+    __syncwarp();
+  } else {
+    const int quad = warp & 3;  // the TMEM lanes (tile rows) this warp may read
+    float* tile = ep + (warp - 2) * EP_FLOATS;
+    int it = 0;
+    for (int t = blockIdx.x; t < g.tiles; t += gridDim.x, ++it) {
+      const int acc = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      bool got = mbar_wait(tfull0 + 8 * acc, use & 1);
+      got = __all_sync(0xffffffffu, got);
+      if (!got) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int sp, bz, m0, n0, kb0, kb1;
+      tile_coords(g, t, sp, bz, m0, n0, kb0, kb1);
+      // each lane locates one of the warp's 32 rows once; the store loop broadcasts them
+      const int my_row = m0 + quad * 32 + lane;
+      long long my_off = -1;
+      if (my_row < g.M)
+        my_off = g.splits > 1 ? (((long long)sp * g.batch + bz) * g.M + my_row) * (long long)g.N
+                              : cidx(g.cb, bz) + cidx(g.cm, my_row);
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%"
+            "22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+              "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+              "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+              "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        // a warp's stores run along a row of C
+        const int n = n0 + c0 + lane;
+        if (g.splits > 1) {
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) {
+            const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
+            if (ro >= 0 && n < g.N) g.part[ro + n] = tile[rr * 33 + lane];
+          }
+        } else {
+          const long long cn = n < g.N ? cidx(g.cn, n) : 0;
+          if (g.beta == 0.0) {
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr) {
+              const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
+              if (ro >= 0 && n < g.N) g.C[ro + cn] = g.alpha * (double)tile[rr * 33 + lane];
+            }
+          } else {
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr) {
+              const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
+              if (ro >= 0 && n < g.N) {
+                double* c = g.C + ro + cn;
+                *c = fma(g.beta, *c, g.alpha * (double)tile[rr * 33 + lane]);
+              }
+            }
+          }
+        }
+        __syncwarp();
+      }
+      // hand the accumulator back to the MMA thread
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
     }
   }
-  if (warp == 0 && lane == 0) {
-    // never leave with copies in flight: the last loads issued must have landed (bounded)
-    for (int kb = std::max(0, g.kblocks - STAGES); kb < g.kblocks; ++kb)
-      if (!mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1)) ok = false;
-  }
-  if (!ok && lane == 0) atomicExch(g.err, 1);
+  if (!ok) atomicExch(g.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
@@ -293,8 +391,6 @@ CUtensorMap make_map(const float* base, int k_pad, int rows_pad, int batch, int 
   return m;
 }
 
-constexpr size_t SMEM_BYTES = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 1) * 8 + 16;
-
 }  // namespace
 
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
@@ -307,7 +403,8 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
     CC_CUDA(cudaGetLastError());
     return;
   }
-  CC_REQUIRE(g.batch <= 65535, CC_ERR_INVALID, "tensor-core contraction: batch too large");
+  CC_REQUIRE((long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN) * g.batch < (1LL << 31), CC_ERR_INVALID,
+             "tensor-core contraction: too many tiles");
   const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
   const int k_pad = (g.K + TK - 1) / TK * TK;
   // the split precision stages [hi|hi|lo] against [hi|lo|hi] along a three times longer k
@@ -332,6 +429,19 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   a.M = g.M;
   a.N = g.N;
   a.kblocks = kk / TK;
+  a.num_m = rowsA / TM;
+  a.num_n = rowsB / TN;
+  a.batch = g.batch;
+  // split k when the output has fewer tiles than SMs and the sum is long: every split is a
+  // tile of its own that writes FP32 partial sums, added in order by a second kernel
+  const long long base_tiles = (long long)a.num_m * a.num_n * g.batch;
+  int splits = 1;
+  if (base_tiles < ex.sm_count && a.kblocks >= 8)
+    splits = (int)std::max<long long>(1, std::min<long long>((ex.sm_count + base_tiles - 1) / base_tiles, a.kblocks / 4));
+  a.kchunk = (a.kblocks + splits - 1) / splits;
+  splits = (a.kblocks + a.kchunk - 1) / a.kchunk;  // no empty split
+  a.splits = splits;
+  a.tiles = (int)(base_tiles * splits);
   a.cm = g.cm;
   a.cn = g.cn;
   a.cb = g.cb;
@@ -339,17 +449,30 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   a.beta = g.beta;
   a.C = g.C;
   a.err = ex.dev_flag;
+  DBuf<double> part;
+  a.part = nullptr;
+  if (splits > 1) {
+    const size_t np = (size_t)splits * g.batch * g.M * g.N;
+    part.alloc(ex.pool, (np + 1) / 2);
+    a.part = reinterpret_cast<float*>(part.p);
+  }
   static bool attr = false;
   if (!attr) {
     CC_CUDA(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     attr = true;
   }
-  dim3 grid(rowsB / TN, rowsA / TM, g.batch);
+  const int grid = std::min(a.tiles, ex.sm_count);  // persistent: at most one CTA per SM
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
   gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
   ex.count();
   CC_CUDA(cudaGetLastError());
+  if (splits > 1) {
+    const size_t tot = (size_t)g.batch * g.M * g.N;
+    tc_splitk_reduce_kernel<<<blocks_for(tot), 256, 0, ex.stream>>>(g, a.part, splits);
+    ex.count();
+    CC_CUDA(cudaGetLastError());
+  }
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
 }
 
