@@ -118,7 +118,9 @@ int cc_ctx_profile(cc_ctx* ctx, int enable);
  * last cc_ctx_profile(ctx, 1). Waits for the recorded launches to finish. */
 int cc_ctx_profile_get(cc_ctx* ctx, const char* tag, uint64_t* launches, double* total_ms, double* flops);
 
-/* A problem resident on the device: copies fock (n x n) and B (naux x n x n), host or device. */
+/* A problem resident on the device: copies fock (n x n) and B (naux x n x n), host or device.
+ * Its device memory comes from the context's pool, so every cc_sys of a context must be
+ * destroyed before the context is. */
 int cc_sys_create(cc_ctx* ctx, int o, int v, int naux, const double* fock, const double* B, cc_sys** out);
 void cc_sys_destroy(cc_sys* sys);
 

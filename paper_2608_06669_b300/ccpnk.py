@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -154,6 +155,7 @@ class Context:
             raise CCError(st, "cc_ctx_create failed")
         self.h = h
         self.device = device
+        self.systems = weakref.WeakSet()  # closed before the context is
 
     @property
     def device_bytes(self) -> int:
@@ -176,6 +178,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            for s in list(getattr(self, "systems", ())):
+                s.close()
             lib().cc_ctx_destroy(self.h)
             self.h = None
 
@@ -192,8 +196,11 @@ class System:
     def __init__(self, ctx: Context, o: int, v: int, naux: int, fock, B):
         keep = []
         h = ctypes.c_void_p()
+        if not getattr(ctx, "h", None):
+            raise CCError(-1, "the context is closed")
         _check(ctx.h, lib().cc_sys_create(ctx.h, o, v, naux, _ptr(fock, keep), _ptr(B, keep), ctypes.byref(h)))
         self.ctx, self.h, self.o, self.v, self.naux = ctx, h, o, v, naux
+        ctx.systems.add(self)
 
     @classmethod
     def from_synth(cls, ctx: Context, s):

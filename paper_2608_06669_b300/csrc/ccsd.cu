@@ -79,11 +79,14 @@ Engine::Engine(const Exec& ex, const System& s) : ex_(ex), s_(s) {
   alloc(Go_, (size_t)o * o);
   alloc(X_, oovv);
   alloc(Y2_, oovv);
-  // ladder workspace: blocks of a with an (a, b, c, d) slab of at most ~512 MB
+  // ladder workspace: blocks of about v/8 values of a (so the half-triangle saving applies),
+  // with an (a, b, c, d) slab of at most ~512 MB
   const double cap = 512.0 * 1024 * 1024;
   const double per_a = 8.0 * (double)v * v * v;
-  ladder_block_ = std::max(1, std::min(v, (int)(cap / std::max(per_a, 1.0))));
+  ladder_block_ = std::max(1, std::min((v + 7) / 8, (int)(cap / std::max(per_a, 1.0))));
   W_.alloc(ex.pool, (size_t)ladder_block_ * v * v * v);
+  // the tangent's stacked factors [dBt_vv ; Bt_vv] and [Bt_vv ; dBt_vv]
+  XsYs_.alloc(ex.pool, 4 * (size_t)P * v * v);
   scratch_.alloc(ex.pool, 64 * 1024);
 }
 
@@ -102,22 +105,31 @@ struct TP {
 
 }  // namespace
 
-void Engine::ladder(const double* Xv, const double* Yv, const double* T, double* R, cc_precision prec) {
-  // R[i][j][a][b] += sum_{P,c,d} X[P][a][c] Y[P][b][d] T[i][j][c][d]
-  const int o = s_.o, v = s_.v, P = s_.P;
+void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* T, double* R, cc_precision prec) {
+  // R[i][j][a][b] += L[i][j][a][b] = sum_{P,c,d} X[P][a][c] Y[P][b][d] T[i][j][c][d].
+  // The caller guarantees that V_{ac,bd} = sum_P X[P][a][c] Y[P][b][d] is symmetric under
+  // (a,c) <-> (b,d); with T[i][j][c][d] = T[j][i][d][c] that makes L[i][j][a][b] = L[j][i][b][a].
+  // So for a block of a only the b >= (start of that block) part of V is built and contracted,
+  // about half of both GEMMs, and the rest of R is read off the mirror.
+  const int o = s_.o, v = s_.v;
   double* X = const_cast<double*>(Xv);
   double* Y = const_cast<double*>(Yv);
   double* Tm = const_cast<double*>(T);
+  double* L = Y2_.val.p;
+  const bool f64 = prec == CC_FP64;
   for (int a0 = 0; a0 < v; a0 += ladder_block_) {
     const int al = std::min(ladder_block_, v - a0);
-    TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {P, al, v}, {(long long)v * v, v, 1});
-    TView W = view(W_.p, "abcd", {al, v, v, v});
-    const bool f64 = prec == CC_FP64;
-    contract(ex_, prec, 1.0, Xa, view(Y, "Pbd", {P, v, v}), 0.0, W, f64 ? "ladder_build.fp64" : "ladder_build.tf32");
-    TView Rv = view_strided(R + (size_t)a0 * v, "ijab", {o, o, al, v}, {(long long)o * v * v, (long long)v * v, v, 1});
-    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 1.0, Rv,
+    const int bl = v - a0;  // b in [a0, v)
+    TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {Paux, al, v}, {(long long)v * v, v, 1});
+    TView Yb = view_strided(Y + (size_t)a0 * v, "Pbd", {Paux, bl, v}, {(long long)v * v, v, 1});
+    TView W = view(W_.p, "abcd", {al, bl, v, v});
+    contract(ex_, prec, 1.0, Xa, Yb, 0.0, W, f64 ? "ladder_build.fp64" : "ladder_build.tf32");
+    TView Lv = view_strided(L + (size_t)a0 * v + a0, "ijab", {o, o, al, bl},
+                            {(long long)o * v * v, (long long)v * v, v, 1});
+    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv,
              f64 ? "ladder_contract.fp64" : "ladder_contract.tf32");
   }
+  k_ladder_mirror_add(ex_, o, v, ladder_block_, L, R);
 }
 
 void Engine::program(bool tan, cc_precision prec, double* rout) {
@@ -242,12 +254,19 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
   bil(1.0, Bvo("Pai"), Bvo("Pbj"), 0.0, R2);
   // particle-particle ladder sum_cd (ac|bd)~ t_ij^cd
   if (!tan) {
-    ladder(Btvv_.val.p, Btvv_.val.p, t_.val.p + ov, r2, prec);
+    ladder(Btvv_.val.p, Btvv_.val.p, P, t_.val.p + ov, r2, prec);
   } else {
-    ladder(Btvv_.val.p, Btvv_.val.p, t_.tan.p + ov, r2, prec);
-    k_fill(ex, oovv, 0.0, Y2_.val.p);
-    ladder(Btvv_.tan.p, Btvv_.val.p, t_.val.p + ov, Y2_.val.p, prec);
-    k_sym_add(ex, o, v, Y2_.val.p, r2, 1.0);  // the (a c)<->(b d) partner of the same term
+    // d[(ac|bd)~ t] = (ac|bd)~ dt + sum_P (dBt_ac Bt_bd + Bt_ac dBt_bd) t; the second factor
+    // pair, stacked along the auxiliary index, is again symmetric under (a,c) <-> (b,d)
+    ladder(Btvv_.val.p, Btvv_.val.p, P, t_.tan.p + ov, r2, prec);
+    const size_t pvv = (size_t)P * v * v;
+    double* Xs = XsYs_.p;
+    double* Ys = XsYs_.p + 2 * pvv;
+    k_copy(ex, pvv, Btvv_.tan.p, Xs);
+    k_copy(ex, pvv, Btvv_.val.p, Xs + pvv);
+    k_copy(ex, pvv, Btvv_.val.p, Ys);
+    k_copy(ex, pvv, Btvv_.tan.p, Ys + pvv);
+    ladder(Xs, Ys, 2 * P, t_.val.p + ov, r2, prec);
   }
   // hole ladder with its quadratic part: W_klij = (ki|lj)~ + sum_cd (kc|ld) t_ij^cd
   TP Woo = dyn(Woo_, 0, "klij", {o, o, o, o});

@@ -41,13 +41,14 @@ class Engine {
     DBuf<double> val, tan;
   };
   void alloc(Pair& x, size_t n);
-  void ladder(const double* Xv, const double* Yv, const double* T, double* R, cc_precision prec);
+  void ladder(const double* Xv, const double* Yv, int Paux, const double* T, double* R, cc_precision prec);
   void program(bool tan, cc_precision prec, double* r_out);
   Exec ex_;
   const System& s_;
   int ladder_block_ = 1;
   Pair t_, u_, Btoo_, Btvv_, Btvo_, gam_, hY_, Ft_, Z_, Wk_, Woo_, Cint_, Dint_, Gv_, Go_, X_, Y2_;
   DBuf<double> W_;        // ladder workspace, ladder_block_ * v^3
+  DBuf<double> XsYs_;     // stacked factors of the tangent ladder
   DBuf<double> scratch_;  // reduction partials
 };
 

@@ -187,6 +187,8 @@ void k_copy(const Exec& ex, size_t n, const double* x, double* y);
 void k_sym_add(const Exec& ex, int o, int v, const double* X, double* out, double beta);
 // u[i][j][a][b] = 2 t[i][j][a][b] - t[j][i][a][b]
 void k_make_u(const Exec& ex, int o, int v, const double* t, double* u);
+// R[i][j][a][b] += L[i][j][a][b] if b >= (a / blk) * blk, else L[j][i][b][a] (the ladder's mirror)
+void k_ladder_mirror_add(const Exec& ex, int o, int v, int blk, const double* L, double* R);
 // L[p][q][r][s] = 2 g[p][q][r][s] - g[p][s][r][q] over an (o v o v) block
 void k_make_L_ovov(const Exec& ex, int o, int v, const double* g, double* L);
 // gamma[P] = sum_k A[P][k][k]

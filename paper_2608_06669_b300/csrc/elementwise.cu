@@ -60,6 +60,20 @@ __global__ void sym_add_kernel(int o, int v, const double* __restrict__ X, doubl
   }
 }
 
+// R[i][j][a][b] += L[i][j][a][b] where b >= start of a's block of size blk, else L[j][i][b][a]
+__global__ void ladder_mirror_add_kernel(int o, int v, int blk, const double* __restrict__ L, double* __restrict__ R) {
+  size_t n = (size_t)o * o * v * v;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    int b = (int)(e % v);
+    size_t r = e / v;
+    int a = (int)(r % v);
+    r /= v;
+    int j = (int)(r % o), i = (int)(r / o);
+    const int bs = (a / blk) * blk;
+    R[e] += (b >= bs) ? L[e] : L[(((size_t)j * o + i) * v + b) * v + a];
+  }
+}
+
 // u[i][j][a][b] = 2 t[i][j][a][b] - t[j][i][a][b]
 __global__ void make_u_kernel(int o, int v, const double* __restrict__ t, double* __restrict__ u) {
   size_t n = (size_t)o * o * v * v;
@@ -327,6 +341,12 @@ void k_sym_add(const Exec& ex, int o, int v, const double* X, double* out, doubl
   size_t n = (size_t)o * o * v * v;
   if (!n) return;
   sym_add_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, X, out, beta);
+  LAUNCH_CHECK();
+}
+void k_ladder_mirror_add(const Exec& ex, int o, int v, int blk, const double* L, double* R) {
+  size_t n = (size_t)o * o * v * v;
+  if (!n) return;
+  ladder_mirror_add_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, blk, L, R);
   LAUNCH_CHECK();
 }
 void k_make_u(const Exec& ex, int o, int v, const double* t, double* u) {
