@@ -83,6 +83,8 @@ typedef struct {
   int inner_max;         /* inner GMRES cap (default 50) */
   int af_direct;         /* 1: invert A_F in the Fock eigenbasis instead of by inner GMRES */
   int verbose;           /* 1: one line per outer iteration on stderr */
+  int ccd;               /* 1: CCD, the paper's level of theory (Sec. Numerics): t1 = 0 throughout and
+                            only the doubles projections are solved */
 } cc_solve_opts;
 
 typedef struct {

@@ -196,10 +196,11 @@ def mp2_guess(fock, B, o):
 # the reference solver: fixed point with the diagonal denominator + DIIS
 # --------------------------------------------------------------------------
 def solve_fp_diis(fock, B, o, t1=None, t2=None, tol=1e-10, maxiter=200, shift=0.0, diis_size=8,
-                  diis_start=2, verbose=False):
+                  diis_start=2, verbose=False, ccd=False):
     """t <- t - R(t) / (D + shift) with D the diagonal-Fock denominator
     (Eq. mo_fixed-point_update; App. D for the shift), Pulay DIIS on
-    (t_new, t_new - t).  Returns (t1, t2, E, history of ||R||)."""
+    (t_new, t_new - t).  ccd=True solves CCD (t1 = 0, doubles projections only).
+    Returns (t1, t2, E, history of ||R||)."""
     v = fock.shape[0] - o
     if t1 is None:
         t1, t2 = mp2_guess(fock, B, o)
@@ -208,8 +209,12 @@ def solve_fp_diis(fock, B, o, t1=None, t2=None, tol=1e-10, maxiter=200, shift=0.
     D2 = (fd[None, None, o:, None] + fd[None, None, None, o:] - fd[:o, None, None, None]
           - fd[None, :o, None, None] + shift)
     vecs, errs, hist = [], [], []
+    if ccd:
+        t1 = np.zeros_like(t1)
     for it in range(maxiter):
         r1, r2, e = residual(fock, B, o, t1, t2)
+        if ccd:
+            r1 = np.zeros_like(r1)
         rn = float(np.sqrt(np.sum(r1 * r1) + np.sum(r2 * r2)))
         hist.append(rn)
         if verbose:

@@ -37,7 +37,8 @@ class SolveOpts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("m_max", ctypes.c_int), ("gamma", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("eta_max", ctypes.c_double), ("level_shift", ctypes.c_double),
                 ("diis_size", ctypes.c_int), ("jvp_fd", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("inner_max", ctypes.c_int), ("af_direct", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("inner_max", ctypes.c_int), ("af_direct", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("ccd", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):

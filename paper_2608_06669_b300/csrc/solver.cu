@@ -261,8 +261,10 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
   auto AFinv = [&](const double* b, double* x) {
     solve_AF(ex, s, b, x, opt.prec, inner_rtol, inner_max, opt.af_direct != 0, &st);
   };
+  const size_t n1 = (size_t)o * v;  // the singles block, dropped in CCD mode
   auto residual = [&](const double* tt, double* rr, double* e_host) -> double {
     eng.value(tt, rr, dev.p + 1, CC_FP64);
+    if (opt.ccd) k_fill(ex, n1, 0.0, rr);
     st.residual_evals++;
     k_dot(ex, n, rr, rr, dev.p, scratch);
     double hv[2];
@@ -278,6 +280,8 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     k_fill(ex, (size_t)o * v, 0.0, r.p);
     k_scale(ex, n, -1.0, r.p);
     AFinv(r.p, t);
+  } else if (opt.ccd) {
+    k_fill(ex, n1, 0.0, t);
   }
 
   double energy = 0.0, rn = 0.0, rn_prev = 0.0, eta_prev = opt.eta_max;
@@ -424,6 +428,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
           eng.tangent(q, target, opt.prec);
         }
         st.jvps++;
+        if (opt.ccd) k_fill(ex, n1, 0.0, target);
         if (pre) AFinv(jq.p, w);
       };
       DBuf<double> delta(ex.pool, n);

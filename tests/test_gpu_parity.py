@@ -191,6 +191,24 @@ def test_solvers_reach_the_oracle_root(ctx, method):
     assert abs(eq - rep["energy"]) < 1e-10
 
 
+@pytest.mark.parametrize("method", ["pnk", "fp_diis"])
+def test_ccd_mode_reaches_the_paper_ccd_root(ctx, method):
+    """CCD (the paper's level of theory): the GPU root is a root of the paper's own CCD
+    working equations (App. A.1, with the readings of its misprints) and its energy equals
+    the oracle's CCD solve."""
+    from oracle import ccd_paper
+
+    s = synth.workload("o5v20_canonical")
+    _, q2, e_ref, hist = cc.solve_fp_diis(s.fock, s.B, s.o, tol=1e-11, maxiter=300, ccd=True)
+    assert hist[-1] < 1e-11
+    t1, t2, rep = gpu_system(ctx, s).solve(method, "fp64", ccd=1, max_outer=400)
+    assert rep["status_code"] == 0, rep
+    assert np.all(t1 == 0.0)
+    assert abs(rep["energy"] - e_ref) < 1e-8
+    r = ccd_paper.ccd_residual(s.fock, s.B, s.o, t2)
+    assert np.sqrt((r ** 2).sum()) < 1e-8
+
+
 def test_pnk_is_gauge_invariant(ctx):
     """The same problem in a Haar-rotated gauge: PNK lands on the same energy (App. A.2)."""
     s = synth.workload("o5v20_canonical")

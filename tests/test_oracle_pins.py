@@ -208,6 +208,23 @@ def test_jvp_stencil_is_exact():
     assert errs[1] < 0.2 * errs[0]
 
 
+@pytest.mark.parametrize("gauge", ["canonical", "haar"])
+def test_paper_ccd_equations(gauge):
+    """The paper's own CCD working equations (App. A.1), with the readings of its three
+    misprints, equal the oracle's doubles residual at t1 = 0 in any gauge; the equations as
+    printed do not (which is what makes the readings necessary)."""
+    from oracle import ccd_paper
+
+    o, v, naux = 3, 5, 6
+    s = synth.make_system(o, v, naux, seed=4, gauge=gauge)
+    _, t2 = synth.random_amplitudes(np.random.default_rng(1), o, v, 0.1, 0.1)
+    _, r2, _ = cc.residual(s.fock, s.B, o, np.zeros((o, v)), t2)
+    read = ccd_paper.ccd_residual(s.fock, s.B, o, t2)
+    assert _norm(read - r2) < 1e-13 * _norm(r2)
+    printed = ccd_paper.ccd_residual(s.fock, s.B, o, t2, literal=True)
+    assert _norm(printed - r2) > 1e-4 * _norm(r2)
+
+
 def test_residual_symmetry():
     """P7: R_ij^ab = R_ji^ba for symmetric amplitudes."""
     o, v, naux = 3, 5, 7
