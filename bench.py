@@ -334,8 +334,77 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kernels(args):
+    """Per-kernel rates on one workload: an FP64 residual and the tangent programs in the
+    tensor-core precisions, timed by the library's tagged kernel timer (CUDA events on the
+    context's stream), then capped solves with several methods. Used for the large and the
+    near-degenerate workloads, where the default bench line would take too long."""
+    import numpy as np
+    import torch
+
+    from paper_2608_06669_b300 import ccpnk, synth
+
+    s = synth.workload(args.kernels)
+    o, v, P = s.o, s.v, s.naux
+    ctx = ccpnk.Context(0)
+    g = ccpnk.System.from_synth(ctx, s)
+    rng = np.random.default_rng(0)
+    t1 = torch.zeros((o, v), dtype=torch.float64, device="cuda")
+    t2 = torch.from_numpy(synth.random_amplitudes(rng, o, v, 0.02, 0.02)[1]).cuda()
+    peaks, _ = measured_peaks()
+    tf32_peak = peaks["bf16_tflops"] * TF32_RATIO
+    out = {"workload": args.kernels, "o": o, "v": v, "naux": P}
+
+    def rate(tag):
+        n, ms, fl = ctx.profile_get(tag)
+        return {"launches": n, "ms": ms, "tflops": fl / (ms / 1e3) / 1e12 if ms > 0 else None}
+
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.residual(t1, t2, prec="fp64")
+    torch.cuda.synchronize()
+    t_res = time.perf_counter() - t0
+    out["fp64_residual_s"] = t_res
+    out["fp64_ladder_build"] = rate("ladder_build.fp64")
+    out["fp64_ladder_contract"] = rate("ladder_contract.fp64")
+    full = (2 * P + 2 * o * o) * v ** 4
+    out["fp64_residual_ladder_equiv_tflops"] = full / t_res / 1e12
+    out["fp64_peak_tflops"] = FP64_PEAK_TFLOPS
+    for prec in ("tf32x3", "tf32"):
+        ctx.profile(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.jvp(t1, t2, t1, t2, prec=prec)
+        torch.cuda.synchronize()
+        out[f"{prec}_jvp_incl_fp64_value_s"] = time.perf_counter() - t0
+        out[f"{prec}_ladder_build"] = rate("ladder_build.tf32")
+        out[f"{prec}_ladder_contract"] = rate("ladder_contract.tf32")
+    ctx.profile(False)
+    out["tf32_peak_tflops"] = tf32_peak
+    print(json.dumps({"metric": METRIC, "mode": "kernels", **out}), flush=True)
+    # capped solves, one line each so that a partial run still reports
+    for meth, prec, extra in (("pnk", "tf32x3", {}), ("nk", "tf32x3", {}),
+                              ("fp_diis", "fp64", {"level_shift": args.shift}), ("pnk", "fp64", {})):
+        if prec == "fp64" and meth == "pnk" and args.no_fp64_solve:
+            continue
+        t0 = time.perf_counter()
+        _, _, rep = g.solve(meth, prec, af_direct=1, max_seconds=args.solve_seconds,
+                            max_outer=args.max_newton if meth != "fp_diis" else 10 * args.max_newton, **extra)
+        rep["wall_s"] = time.perf_counter() - t0
+        rep["jvps_per_newton"] = rep["jvps"] / max(rep["newton_iters"], 1)
+        keep = ("energy", "res_norm", "newton_iters", "residual_evals", "jvps", "jvps_per_newton", "status_code",
+                "wall_s")
+        print(json.dumps({"mode": "kernels.solve", "workload": args.kernels, "method": meth, "prec": prec,
+                          **extra, **{k: rep[k] for k in keep}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--kernels", default="", help="per-kernel rates and capped solves on this workload instead")
+    ap.add_argument("--shift", type=float, default=0.2, help="FP+DIIS level shift in --kernels")
+    ap.add_argument("--no-fp64-solve", action="store_true")
+    ap.add_argument("--solve-seconds", type=float, default=120.0, help="wall-time cap of each solve in --kernels")
     ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests instead")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--serve-fp64", type=int, default=8, help="requests the FP64 pass of --serve runs")
@@ -352,6 +421,8 @@ def main():
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.kernels:
+        run_kernels(args)
     else:
         run_ours(args)
 

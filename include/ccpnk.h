@@ -85,6 +85,8 @@ typedef struct {
   int verbose;           /* 1: one line per outer iteration on stderr */
   int ccd;               /* 1: CCD, the paper's level of theory (Sec. Numerics): t1 = 0 throughout and
                             only the doubles projections are solved */
+  double max_seconds;    /* > 0: stop with CC_ERR_NOT_CONVERGED once a solve has run this long
+                            (checked between outer iterations) */
 } cc_solve_opts;
 
 typedef struct {

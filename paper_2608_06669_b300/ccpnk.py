@@ -38,7 +38,7 @@ class SolveOpts(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("eta_max", ctypes.c_double), ("level_shift", ctypes.c_double),
                 ("diis_size", ctypes.c_int), ("jvp_fd", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("inner_max", ctypes.c_int), ("af_direct", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("ccd", ctypes.c_int)]
+                ("ccd", ctypes.c_int), ("max_seconds", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):

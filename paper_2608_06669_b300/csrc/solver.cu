@@ -262,6 +262,10 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     solve_AF(ex, s, b, x, opt.prec, inner_rtol, inner_max, opt.af_direct != 0, &st);
   };
   const size_t n1 = (size_t)o * v;  // the singles block, dropped in CCD mode
+  auto out_of_time = [&]() {
+    return opt.max_seconds > 0 &&
+           std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > opt.max_seconds;
+  };
   auto residual = [&](const double* tt, double* rr, double* e_host) -> double {
     eng.value(tt, rr, dev.p + 1, CC_FP64);
     if (opt.ccd) k_fill(ex, n1, 0.0, rr);
@@ -303,6 +307,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
       if (opt.verbose) fprintf(stderr, "[ccpnk] fp+diis it %3d  |R| %.3e  E %.12f\n", it, rn, energy);
       if (!std::isfinite(rn) || rn > 1e8) { status = CC_ERR_DIVERGED; break; }
       if (rn < opt.tol) { status = CC_OK; break; }
+      if (out_of_time()) break;
       st.newton_iters++;
       // e = -R / (D + shift), t_new = t + e
       k_denom_divide(ex, o, v, fdiag.p, opt.level_shift, r.p, r.p + (size_t)o * v, tmp.p, tmp.p + (size_t)o * v, -1.0);
@@ -386,6 +391,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
       if (opt.verbose) fprintf(stderr, "[ccpnk] newton %3d  |R| %.3e  E %.12f  eta %.2e\n", k, rn, energy, eta_prev);
       if (!std::isfinite(rn) || rn > 1e8) { status = CC_ERR_DIVERGED; break; }
       if (rn < opt.tol) { status = CC_OK; break; }
+      if (out_of_time()) break;
       st.newton_iters++;
       if (opt.method == CC_INK) {
         // t <- t + A_F^{-1}(-r)
