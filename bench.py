@@ -306,7 +306,7 @@ def run_serve(args):
             if wait > 0:
                 time.sleep(wait)
             tickets.append(srv.submit(s.o, s.v, s.naux, s.fock, s.B, "pnk", prec, af_direct=1,
-                                      max_outer=args.max_newton))
+                                      max_outer=args.max_newton, max_seconds=args.solve_seconds))
         results = {}
         while len(results) < len(tickets):
             for t in tickets:
