@@ -52,8 +52,11 @@ typedef enum {
   CC_FP64 = 0,          /* every contraction in FP64 (FMA pipe) */
   CC_MIXED_TF32 = 1,    /* contractions of JVPs / inner solves on tcgen05 TF32, FP32 accumulate */
   CC_MIXED_BF16X3 = 2,  /* reserved: 3-pass BF16-split contractions (returns CC_ERR_INVALID today) */
-  CC_MIXED_TF32X3 = 3   /* 3-pass TF32 split: x = hi + lo, a b ~ hi hi + hi lo + lo hi on tcgen05,
+  CC_MIXED_TF32X3 = 3,  /* 3-pass TF32 split: x = hi + lo, a b ~ hi hi + hi lo + lo hi on tcgen05,
                            FP32 accumulate (about FP32 accuracy at a third of the TF32 rate) */
+  CC_DF64 = 4           /* double-float: FP64 operands as FP32 pairs on the FP32 pipe (error-free
+                           products, two-sum accumulation; about 48 significant bits), for the
+                           residual when FP64 FMA throughput is the limit */
 } cc_precision;
 
 typedef enum {
@@ -87,6 +90,7 @@ typedef struct {
                             only the doubles projections are solved */
   double max_seconds;    /* > 0: stop with CC_ERR_NOT_CONVERGED once a solve has run this long
                             (checked between outer iterations) */
+  int outer_prec;        /* precision of the outer residual: CC_FP64 (default) or CC_DF64 */
 } cc_solve_opts;
 
 typedef struct {

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libccpnk.so")
 CC_OK, CC_PENDING = 0, 1
 STATUS = {-1: "CC_ERR_INVALID", -2: "CC_ERR_OOM", -3: "CC_ERR_NOT_CONVERGED", -4: "CC_ERR_DIVERGED",
           -5: "CC_ERR_CUDA", -6: "CC_ERR_TIMEOUT"}
-PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3}
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3, "df64": 4}
 METHOD = {"fp_diis": 0, "nk": 1, "pnk": 2, "ink": 3}
 
 
@@ -38,7 +38,7 @@ class SolveOpts(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("eta_max", ctypes.c_double), ("level_shift", ctypes.c_double),
                 ("diis_size", ctypes.c_int), ("jvp_fd", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("inner_max", ctypes.c_int), ("af_direct", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("ccd", ctypes.c_int), ("max_seconds", ctypes.c_double)]
+                ("ccd", ctypes.c_int), ("max_seconds", ctypes.c_double), ("outer_prec", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):

@@ -184,8 +184,8 @@ Engine& engine(cc_sys* sys) {
 }
 
 void check_prec(cc_precision p) {
-  CC_REQUIRE(p == CC_FP64 || p == CC_MIXED_TF32 || p == CC_MIXED_TF32X3, CC_ERR_INVALID,
-             "precision not available (CC_FP64, CC_MIXED_TF32 and CC_MIXED_TF32X3 are)");
+  CC_REQUIRE(p == CC_FP64 || p == CC_MIXED_TF32 || p == CC_MIXED_TF32X3 || p == CC_DF64, CC_ERR_INVALID,
+             "precision not available (CC_FP64, CC_MIXED_TF32, CC_MIXED_TF32X3 and CC_DF64 are)");
 }
 
 // [t1 | t2] with t2 symmetrised: T2 only depends on t_ij^ab + t_ji^ba

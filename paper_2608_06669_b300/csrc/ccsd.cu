@@ -116,18 +116,19 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
   double* Y = const_cast<double*>(Yv);
   double* Tm = const_cast<double*>(T);
   double* L = Y2_.val.p;
-  const bool f64 = prec == CC_FP64;
+  const char* tb = prec == CC_FP64 ? "ladder_build.fp64" : prec == CC_DF64 ? "ladder_build.df64" : "ladder_build.tf32";
+  const char* tc = prec == CC_FP64 ? "ladder_contract.fp64"
+                                   : prec == CC_DF64 ? "ladder_contract.df64" : "ladder_contract.tf32";
   for (int a0 = 0; a0 < v; a0 += ladder_block_) {
     const int al = std::min(ladder_block_, v - a0);
     const int bl = v - a0;  // b in [a0, v)
     TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {Paux, al, v}, {(long long)v * v, v, 1});
     TView Yb = view_strided(Y + (size_t)a0 * v, "Pbd", {Paux, bl, v}, {(long long)v * v, v, 1});
     TView W = view(W_.p, "abcd", {al, bl, v, v});
-    contract(ex_, prec, 1.0, Xa, Yb, 0.0, W, f64 ? "ladder_build.fp64" : "ladder_build.tf32");
+    contract(ex_, prec, 1.0, Xa, Yb, 0.0, W, tb);
     TView Lv = view_strided(L + (size_t)a0 * v + a0, "ijab", {o, o, al, bl},
                             {(long long)o * v * v, (long long)v * v, v, 1});
-    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv,
-             f64 ? "ladder_contract.fp64" : "ladder_contract.tf32");
+    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc);
   }
   k_ladder_mirror_add(ex_, o, v, ladder_block_, L, R);
 }

@@ -149,6 +149,118 @@ __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float variant: the same tiles, with every FP64 operand split into an FP32 pair
+// x = hi + lo (hi = fl(x), lo = fl(x - hi), about 48 significant bits) and every
+// multiply-add done on the FP32 pipe, which a B300 runs about 60x faster than FP64:
+//   product   a b = p + e exactly up to the dropped lo*lo term: p = fl(ah bh),
+//             e = fma(ah, bh, -p) + ah bl + al bh   (Dekker's error-free product via FMA)
+//   sum       (sh, sl) += (p, e) with Knuth's two-sum on the high parts, lows added
+// The explicit __fadd_rn / __fmul_rn keep the compiler from fusing the two-sum steps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_mac(float2 a, float2 b, float& sh, float& sl) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = __fadd_rn(sh, p);
+  const float bv = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = s;
+}
+
+__device__ __forceinline__ float2 df_split(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
+__global__ void __launch_bounds__(NT, 2) gemm_df64_kernel(GemmArgs g) {
+  __shared__ float2 As[BK][BM + 1];
+  __shared__ float2 Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int split = blockIdx.z % g.splits;
+  const int kbeg = split * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  int a_mm[4], a_kk[4], b_nn[4], b_kk[4];
+  long long a_moff[4], b_noff[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int e = tid + NT * r;
+    if (g.a_kfast) { a_kk[r] = e % BK; a_mm[r] = e / BK; }
+    else           { a_mm[r] = e % BM; a_kk[r] = e / BM; }
+    if (g.b_kfast) { b_kk[r] = e % BK; b_nn[r] = e / BK; }
+    else           { b_nn[r] = e % BN; b_kk[r] = e / BN; }
+    int m = m0 + a_mm[r], n = n0 + b_nn[r];
+    a_moff[r] = m < g.M ? cidx(g.am, m) : -1;
+    b_noff[r] = n < g.N ? cidx(g.bn, n) : -1;
+  }
+  for (int bz = blockIdx.z / g.splits; bz < g.batch; bz += gridDim.z / g.splits) {
+    const double* A = g.A + cidx(g.ab, bz);
+    const double* B = g.B + cidx(g.bb, bz);
+    float sh[4][4], sl[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.0f;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int k = k0 + a_kk[r];
+        As[a_kk[r]][a_mm[r]] = df_split((a_moff[r] >= 0 && k < kend) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0);
+        int kb = k0 + b_kk[r];
+        Bs[b_kk[r]][b_nn[r]] = df_split((b_noff[r] >= 0 && kb < kend) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        float2 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_mac(a[i], b[j], sh[i][j], sl[i][j]);
+      }
+      __syncthreads();
+    }
+    if (g.splits > 1) {
+      double* P = g.part + ((size_t)split * g.batch + bz) * (size_t)g.M * g.N;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int n = n0 + tx + 16 * j;
+          if (n < g.N) P[(size_t)m * g.N + n] = (double)sh[i][j] + (double)sl[i][j];
+        }
+      }
+      continue;
+    }
+    double* C = g.C + cidx(g.cb, bz);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int m = m0 + ty + 16 * i;
+      if (m >= g.M) continue;
+      long long cm = cidx(g.cm, m);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int n = n0 + tx + 16 * j;
+        if (n >= g.N) continue;
+        double* c = C + cm + cidx(g.cn, n);
+        double val = g.alpha * ((double)sh[i][j] + (double)sl[i][j]);
+        if (g.beta != 0.0) val = fma(g.beta, *c, val);
+        *c = val;
+      }
+    }
+  }
+}
+
 // C = alpha * sum_s part[s] + beta * C, the splits added in order
 __global__ void splitk_reduce_kernel(GemmArgs g) {
   const size_t per = (size_t)g.M * g.N;
@@ -228,7 +340,7 @@ long long inner_stride(const CIdx& c) { return (c.e1 == 1 && c.e2 == 1) ? c.s0 :
 
 void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
-  if (prec != CC_FP64) {
+  if (prec != CC_FP64 && prec != CC_DF64) {
     gemm_tc(ex, prec, g, tag);
     return;
   }
@@ -253,7 +365,8 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
   dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)(zb * splits));
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
-  gemm_f64_kernel<<<grid, NT, 0, ex.stream>>>(g);
+  if (prec == CC_DF64) gemm_df64_kernel<<<grid, NT, 0, ex.stream>>>(g);
+  else gemm_f64_kernel<<<grid, NT, 0, ex.stream>>>(g);
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {

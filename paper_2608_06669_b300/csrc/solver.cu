@@ -262,12 +262,13 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     solve_AF(ex, s, b, x, opt.prec, inner_rtol, inner_max, opt.af_direct != 0, &st);
   };
   const size_t n1 = (size_t)o * v;  // the singles block, dropped in CCD mode
+  const cc_precision outer = opt.outer_prec == CC_DF64 ? CC_DF64 : CC_FP64;
   auto out_of_time = [&]() {
     return opt.max_seconds > 0 &&
            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > opt.max_seconds;
   };
   auto residual = [&](const double* tt, double* rr, double* e_host) -> double {
-    eng.value(tt, rr, dev.p + 1, CC_FP64);
+    eng.value(tt, rr, dev.p + 1, outer);
     if (opt.ccd) k_fill(ex, n1, 0.0, rr);
     st.residual_evals++;
     k_dot(ex, n, rr, rr, dev.p, scratch);
@@ -427,7 +428,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
           double delta = 1.4901161193847656e-08 * (1.0 + tnorm);
           k_copy(ex, n, t, tp.p);
           k_axpby(ex, n, delta, q, 1.0, tp.p);
-          eng.value(tp.p, target, nullptr, CC_FP64);
+          eng.value(tp.p, target, nullptr, outer);
           st.residual_evals++;
           k_axpby(ex, n, -1.0 / delta, r.p, 1.0 / delta, target);
         } else {

@@ -97,6 +97,36 @@ def test_residual_parity_workload(ctx, name):
     assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
 
 
+@pytest.mark.parametrize("name", ["o5v20_canonical", "o10v90_rotated"])
+def test_double_float_residual_and_jvp_parity(ctx, name):
+    """CC_DF64 (FP64 operands as FP32 pairs on the FP32 pipe) meets the FP64 bound."""
+    s = synth.workload(name)
+    o, v = s.o, s.v
+    t1, t2 = cc.mp2_guess(s.fock, s.B, o)
+    p1, p2 = synth.random_amplitudes(np.random.default_rng(8), o, v, 0.01, 0.01)
+    t1, t2 = t1 + p1, t2 + p2
+    g = gpu_system(ctx, s)
+    r1, r2, e = g.residual(t1, t2, prec="df64")
+    q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
+    scale = max(np.abs(q1).max(), np.abs(q2).max())
+    assert np.abs(r1 - q1).max() <= TOL64 * scale and np.abs(r2 - q2).max() <= TOL64 * scale
+    assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
+    if name == "o5v20_canonical":
+        d1, d2 = synth.random_amplitudes(np.random.default_rng(9), o, v, 0.01, 0.01)
+        j1, j2 = g.jvp(t1, t2, d1, d2, prec="df64")
+        k1, k2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+        scale = max(np.abs(k1).max(), np.abs(k2).max())
+        assert np.abs(j1 - k1).max() <= TOL64 * scale and np.abs(j2 - k2).max() <= TOL64 * scale
+
+
+def test_double_float_outer_residual_solve(ctx):
+    s = synth.workload("o10v90_rotated")
+    ref = _golden()["o10v90_rotated"]["e_corr"]
+    _, _, rep = gpu_system(ctx, s).solve("pnk", "tf32x3", af_direct=1, outer_prec=4)
+    assert rep["status_code"] == 0, rep
+    assert abs(rep["energy"] - ref) < 1e-8
+
+
 @pytest.mark.parametrize("o,v,naux,gauge", [(1, 2, 2, "haar"), (2, 4, 5, "haar"), (4, 9, 11, "small"),
                                              (7, 33, 20, "haar")])
 def test_jvp_parity(ctx, o, v, naux, gauge):
