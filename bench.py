@@ -224,6 +224,15 @@ def run_ours(args):
     _, _, rep_gm = g.solve(method="pnk", prec=args.prec, af_direct=0)
     t_gmres = time.perf_counter() - t0
 
+    # the same solves with the outer residual in double-float (FP32 pairs on the FP32 pipe),
+    # and a solve done entirely in double-float
+    t0 = time.perf_counter()
+    _, _, rep_df = g.solve(method="pnk", prec=args.prec, af_direct=kw["af_direct"], outer_prec=4)
+    t_df_outer = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, _, rep_dfall = g.solve(method="pnk", prec="df64", af_direct=kw["af_direct"], outer_prec=4)
+    t_df_all = time.perf_counter() - t0
+
     # end to end through the C ABI with host buffers: upload the problem, solve, read back
     n = s.o + s.v
     e2e_times = []
@@ -273,6 +282,10 @@ def run_ours(args):
         "fp64_pnk_s": t_fp64,
         "speedup_mixed_vs_fp64": t_fp64 / t_max,
         "mixed_pnk_af_gmres_s": t_gmres,
+        "mixed_pnk_df64_outer_s": t_df_outer,
+        "df64_pnk_s": t_df_all,
+        "solve_df64_outer": {k: rep_df[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
+        "solve_df64": {k: rep_dfall[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
         "solve_af_gmres": {k: rep_gm[k] for k in ("energy", "res_norm", "newton_iters", "jvps", "af_applies")},
         "solve": {k: reports[-1][k] for k in ("energy", "res_norm", "newton_iters", "residual_evals", "jvps",
                                                "af_applies", "krylov_iters")},
