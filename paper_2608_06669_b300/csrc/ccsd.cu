@@ -119,16 +119,36 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
   const char* tb = prec == CC_FP64 ? "ladder_build.fp64" : prec == CC_DF64 ? "ladder_build.df64" : "ladder_build.tf32";
   const char* tc = prec == CC_FP64 ? "ladder_contract.fp64"
                                    : prec == CC_DF64 ? "ladder_contract.df64" : "ladder_contract.tf32";
+  const bool tensor = prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3;
+  // tensor cores: the slab goes straight from the first GEMM's epilogue, as TF32 segments in
+  // the K-major layout the second GEMM loads, to the second GEMM (no FP64 round trip)
+  const int nseg = prec == CC_MIXED_TF32X3 ? 3 : 1;
+  const long long kpad = ((long long)v * v + 31) / 32 * 32, kk = nseg * kpad;
+  const int rows_pad = (ladder_block_ * v + 255) / 256 * 256;
+  if (tensor && !W2_.p) {
+    W2_.alloc(ex_.pool, (size_t)rows_pad * 3 * kpad / 2 + 1);  // sized for three segments
+    CC_CUDA(cudaMemsetAsync(W2_.p, 0, W2_.n * sizeof(double), ex_.stream));  // zero k padding
+  }
+  float* W2 = reinterpret_cast<float*>(W2_.p);
   for (int a0 = 0; a0 < v; a0 += ladder_block_) {
     const int al = std::min(ladder_block_, v - a0);
     const int bl = v - a0;  // b in [a0, v)
     TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {Paux, al, v}, {(long long)v * v, v, 1});
     TView Yb = view_strided(Y + (size_t)a0 * v, "Pbd", {Paux, bl, v}, {(long long)v * v, v, 1});
-    TView W = view(W_.p, "abcd", {al, bl, v, v});
-    contract(ex_, prec, 1.0, Xa, Yb, 0.0, W, tb);
     TView Lv = view_strided(L + (size_t)a0 * v + a0, "ijab", {o, o, al, bl},
                             {(long long)o * v * v, (long long)v * v, v, 1});
-    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc);
+    TView W = view(W_.p, "abcd", {al, bl, v, v});
+    if (!tensor) {
+      contract(ex_, prec, 1.0, Xa, Yb, 0.0, W, tb);
+      contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc);
+      continue;
+    }
+    // W2[(a,b)][s * kpad + c v + d]: the strides below count floats of W2
+    StagedOut so{W2, kpad, nseg, nseg == 3 ? 0b010 : 0};
+    TView Ws = view_strided(nullptr, "abcd", {al, bl, v, v}, {(long long)bl * kk, kk, v, 1});
+    contract(ex_, prec, 1.0, Xa, Yb, 0.0, Ws, tb, &so, nullptr);
+    StagedIn sb{W2, rows_pad, (int)kk};
+    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc, nullptr, &sb);
   }
   k_ladder_mirror_add(ex_, o, v, ladder_block_, L, R);
 }

@@ -132,6 +132,18 @@ struct CIdx {
   long long s0 = 0, s1 = 0, s2 = 0;
 };
 
+// Tensor-core operands kept in staging layout between two contractions: a K-major FP32
+// [rows][nseg * kpad] array whose nseg segments hold the TF32 high part or the low part.
+struct StagedOut {  // C written in that layout (C's strides count floats), beta must be 0
+  float* base;
+  long long kpad;
+  int nseg, seg_lo;  // seg_lo: bit mask of the segments that hold the low part
+};
+struct StagedIn {  // the B operand already staged (rows padded to the tile, zero k padding)
+  const float* base;
+  int rows_pad, kk;  // kk = nseg * kpad floats per row
+};
+
 struct GemmArgs {
   const double* A;
   const double* B;
@@ -145,6 +157,8 @@ struct GemmArgs {
   int splits;            // split-K factor (1: write C directly)
   int kchunk;            // k range per split (multiple of the k slice)
   double* part;          // split-K partials [splits][batch][M][N]
+  const StagedOut* so;   // tensor-core only: C in staging layout
+  const StagedIn* sb;    // tensor-core only: B already staged
 };
 
 // Tensor-core GEMM (gemm_tc.cu): same contract as the FP64 kernel, run on tcgen05.
@@ -174,7 +188,8 @@ TView view_strided(double* p, const char* labels, std::initializer_list<int> ext
 // are batch modes, labels in A and C the row modes, in B and C the column modes, labels in
 // A and B only are summed. prec selects the FP64 FMA kernel or the tensor-core kernel.
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
-              double beta, const TView& C, const char* tag = nullptr);
+              double beta, const TView& C, const char* tag = nullptr, const StagedOut* so = nullptr,
+              const StagedIn* sb = nullptr);
 
 // ---------------------------------------------------------------------------
 // kernels with host launchers (elementwise.cu)

@@ -340,6 +340,7 @@ long long inner_stride(const CIdx& c) { return (c.e1 == 1 && c.e2 == 1) ? c.s0 :
 
 void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  CC_REQUIRE(!((g.so || g.sb) && (prec == CC_FP64 || prec == CC_DF64)), CC_ERR_INVALID, "staged operands need a tensor-core precision");
   if (prec != CC_FP64 && prec != CC_DF64) {
     gemm_tc(ex, prec, g, tag);
     return;
@@ -383,7 +384,7 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
 }  // namespace
 
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
-              double beta, const TView& C, const char* tag) {
+              double beta, const TView& C, const char* tag, const StagedOut* so, const StagedIn* sb) {
   auto find = [](const TView& t, char l) {
     for (int d = 0; d < t.nd; ++d)
       if (t.lab[d] == l) return d;
@@ -459,10 +460,13 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
   g.alpha = alpha;
   g.beta = beta;
   g.splits = 1;
+  g.so = so;
+  g.sb = sb;
   g.a_kfast = gk.empty() ? 1 : (inner_stride(g.ak) == 1);
   g.b_kfast = gk.empty() ? 1 : (inner_stride(g.bk) == 1 && inner_stride(g.bn) != 1);
 
   const int nl = (int)loops.size();
+  CC_REQUIRE(nl == 0 || (!so && !sb), CC_ERR_INVALID, "staged operands need a contraction without spilled modes");
   std::vector<int> idx(nl, 0);
   while (true) {
     GemmArgs gi = g;

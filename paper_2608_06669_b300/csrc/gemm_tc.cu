@@ -44,6 +44,14 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// writes x into the staging segments of one element: the TF32 high part, or the low part.
+// All in FP32: x - tf32(x) is exact in FP32, and nothing here touches the FP64 pipe.
+__device__ __forceinline__ void store_staged(float* p, long long kpad, int nseg, int seglo, float x) {
+  const float hi = to_tf32(x);
+  const float lo = to_tf32(__fsub_rn(x, hi));
+  for (int s = 0; s < nseg; ++s) p[(long long)s * kpad] = ((seglo >> s) & 1) ? lo : hi;
+}
+
 // out[b][r][s * k_pad + k] for r < rows_pad, k < k_pad and the nseg segments s of a row
 // (FP32, TF32-rounded, zero outside rows x K). seg_lo is a bit mask of the segments that hold
 // the low part lo = tf32(x - hi) instead of the high part hi = tf32(x); one segment with
@@ -69,8 +77,10 @@ __global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix
   }
 }
 
-// split-k: C = alpha * sum_s part[s] + beta * C, the splits added in a fixed order
-__global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int splits) {
+// split-k: C = alpha * sum_s part[s] + beta * C, the splits added in a fixed order (or, with
+// a staged output, alpha * sum written as TF32 segments)
+__global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int splits, float* Cs,
+                                        long long kpad, int nseg, int seglo) {
   const size_t tot = (size_t)g.batch * g.M * g.N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     int n = (int)(e % g.N);
@@ -79,8 +89,13 @@ __global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ pa
     int b = (int)(r / g.M);
     double s = 0.0;
     for (int q = 0; q < splits; ++q) s += (double)part[(size_t)q * tot + e];
-    double* c = g.C + cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
-    *c = g.beta == 0.0 ? g.alpha * s : fma(g.beta, *c, g.alpha * s);
+    const long long off = cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
+    if (Cs) {
+      store_staged(Cs + off, kpad, nseg, seglo, (float)(g.alpha * s));
+    } else {
+      double* c = g.C + off;
+      *c = g.beta == 0.0 ? g.alpha * s : fma(g.beta, *c, g.alpha * s);
+    }
   }
 }
 
@@ -105,6 +120,9 @@ struct TcArgs {
   double* C;
   float* part;  // split-k partial sums [splits][batch][M][N] (splits > 1)
   int* err;
+  float* Cs;    // non-null: C in staging layout (offsets from cm/cn/cb count floats)
+  long long cs_kpad;
+  int cs_nseg, cs_seglo;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -290,6 +308,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   } else {
     const int quad = warp & 3;  // the TMEM lanes (tile rows) this warp may read
+    const float alpha_f = (float)g.alpha;
     float* tile = ep + (warp - 2) * EP_FLOATS;
     int it = 0;
     for (int t = blockIdx.x; t < g.tiles; t += gridDim.x, ++it) {
@@ -330,6 +349,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int rr = 0; rr < 32; ++rr) {
             const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
             if (ro >= 0 && n < g.N) g.part[ro + n] = tile[rr * 33 + lane];
+          }
+        } else if (g.Cs) {
+          const long long cn = n < g.N ? cidx(g.cn, n) : 0;
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
+            if (ro >= 0 && n < g.N)
+              store_staged(g.Cs + ro + cn, g.cs_kpad, g.cs_nseg, g.cs_seglo, alpha_f * tile[rr * 33 + lane]);
           }
         } else {
           const long long cn = n < g.N ? cidx(g.cn, n) : 0;
@@ -410,7 +437,7 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   // the split precision stages [hi|hi|lo] against [hi|lo|hi] along a three times longer k
   const int nseg = prec == CC_MIXED_TF32X3 ? 3 : 1;
   const int kk = nseg * k_pad;
-  const size_t nA = (size_t)g.batch * rowsA * kk, nB = (size_t)g.batch * rowsB * kk;
+  const size_t nA = (size_t)g.batch * rowsA * kk, nB = g.sb ? 0 : (size_t)g.batch * rowsB * kk;
   DBuf<double> stA(ex.pool, (nA + 1) / 2), stB(ex.pool, (nB + 1) / 2);
   float* fA = reinterpret_cast<float*>(stA.p);
   float* fB = reinterpret_cast<float*>(stB.p);
@@ -419,12 +446,22 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   gather_kernel<<<blocks_for(eA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, nseg,
                                                         nseg == 3 ? 0b100 : 0, fA);
   ex.count();
-  gather_kernel<<<blocks_for(eB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad, nseg,
-                                                        nseg == 3 ? 0b010 : 0, fB);
-  ex.count();
+  int rowsBmap = rowsB;
+  if (g.sb) {
+    // B was written in staging layout by an earlier contraction
+    CC_REQUIRE(g.batch == 1 && g.sb->kk == kk && g.sb->rows_pad >= rowsB && g.sb->rows_pad % TN == 0,
+               CC_ERR_INVALID, "staged operand does not match the contraction");
+    fB = const_cast<float*>(g.sb->base);
+    rowsBmap = g.sb->rows_pad;
+  } else {
+    gather_kernel<<<blocks_for(eB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad, nseg,
+                                                          nseg == 3 ? 0b010 : 0, fB);
+    ex.count();
+  }
   CC_CUDA(cudaGetLastError());
+  CC_REQUIRE(!g.so || g.beta == 0.0, CC_ERR_INVALID, "a staged output cannot accumulate");
   CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM);
-  CUtensorMap mB = make_map(fB, kk, rowsB, g.batch, TN);
+  CUtensorMap mB = make_map(fB, kk, rowsBmap, g.batch, TN);
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
@@ -449,6 +486,10 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   a.beta = g.beta;
   a.C = g.C;
   a.err = ex.dev_flag;
+  a.Cs = g.so ? g.so->base : nullptr;
+  a.cs_kpad = g.so ? g.so->kpad : 0;
+  a.cs_nseg = g.so ? g.so->nseg : 0;
+  a.cs_seglo = g.so ? g.so->seg_lo : 0;
   DBuf<double> part;
   a.part = nullptr;
   if (splits > 1) {
@@ -469,7 +510,8 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {
     const size_t tot = (size_t)g.batch * g.M * g.N;
-    tc_splitk_reduce_kernel<<<blocks_for(tot), 256, 0, ex.stream>>>(g, a.part, splits);
+    tc_splitk_reduce_kernel<<<blocks_for(tot), 256, 0, ex.stream>>>(g, a.part, splits, a.Cs, a.cs_kpad, a.cs_nseg,
+                                                                     a.cs_seglo);
     ex.count();
     CC_CUDA(cudaGetLastError());
   }
