@@ -232,6 +232,10 @@ def run_ours(args):
     t0 = time.perf_counter()
     _, _, rep_dfall = g.solve(method="pnk", prec="df64", af_direct=kw["af_direct"], outer_prec=4)
     t_df_all = time.perf_counter() - t0
+    # the inner contractions as three BF16 passes (kind::f16) instead of three TF32 passes
+    t0 = time.perf_counter()
+    _, _, rep_bf = g.solve(method="pnk", prec="bf16x3", af_direct=kw["af_direct"], outer_prec=4)
+    t_bf = time.perf_counter() - t0
 
     # end to end through the C ABI with host buffers: upload the problem, solve, read back
     n = s.o + s.v
@@ -269,7 +273,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"tf32x3": "tf32x3+f64", "tf32": "tf32+f64", "fp64": "f64"}[args.prec], "data": "synthetic",
+        "dtype": {"tf32x3": "tf32x3+f64", "bf16x3": "bf16x3+f64", "tf32": "tf32+f64", "fp64": "f64"}[args.prec], "data": "synthetic",
         "config": {"workload": WORKLOAD, "o": s.o, "v": s.v, "naux": s.naux, "gauge": "rotated (off-diagonal f up to 0.1 Eh)",
                    "method": "pnk", "prec": args.prec, "tol": 1e-8, "start": "generalised MP2",
                    "af_inverse": "gmres" if args.af_gmres else "eigenbasis",
@@ -286,6 +290,8 @@ def run_ours(args):
         "df64_pnk_s": t_df_all,
         "solve_df64_outer": {k: rep_df[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
         "solve_df64": {k: rep_dfall[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
+        "mixed_pnk_bf16x3_df64_outer_s": t_bf,
+        "solve_bf16x3_df64_outer": {k: rep_bf[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
         "solve_af_gmres": {k: rep_gm[k] for k in ("energy", "res_norm", "newton_iters", "jvps", "af_applies")},
         "solve": {k: reports[-1][k] for k in ("energy", "res_norm", "newton_iters", "residual_evals", "jvps",
                                                "af_applies", "krylov_iters")},
@@ -384,15 +390,16 @@ def run_kernels(args):
     full = (2 * P + 2 * o * o) * v ** 4
     out["fp64_residual_ladder_equiv_tflops"] = full / t_res / 1e12
     out["fp64_peak_tflops"] = FP64_PEAK_TFLOPS
-    for prec in ("tf32x3", "tf32"):
+    for prec in ("tf32x3", "bf16x3", "tf32"):
         ctx.profile(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.jvp(t1, t2, t1, t2, prec=prec)
         torch.cuda.synchronize()
         out[f"{prec}_jvp_incl_fp64_value_s"] = time.perf_counter() - t0
-        out[f"{prec}_ladder_build"] = rate("ladder_build.tf32")
-        out[f"{prec}_ladder_contract"] = rate("ladder_contract.tf32")
+        sfx = "bf16" if prec == "bf16x3" else "tf32"
+        out[f"{prec}_ladder_build"] = rate(f"ladder_build.{sfx}")
+        out[f"{prec}_ladder_contract"] = rate(f"ladder_contract.{sfx}")
     ctx.profile(False)
     out["tf32_peak_tflops"] = tf32_peak
     print(json.dumps({"metric": METRIC, "mode": "kernels", **out}), flush=True)
@@ -426,7 +433,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "tf32", "fp64"])
+    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "bf16x3", "tf32", "fp64"])
     ap.add_argument("--af-gmres", action="store_true", help="invert A_F by inner GMRES in the timed solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()

@@ -51,7 +51,8 @@ extern "C" {
 typedef enum {
   CC_FP64 = 0,          /* every contraction in FP64 (FMA pipe) */
   CC_MIXED_TF32 = 1,    /* contractions of JVPs / inner solves on tcgen05 TF32, FP32 accumulate */
-  CC_MIXED_BF16X3 = 2,  /* reserved: 3-pass BF16-split contractions (returns CC_ERR_INVALID today) */
+  CC_MIXED_BF16X3 = 2,  /* 3-pass BF16 split: x = hi + lo in BF16, a b ~ hi hi + hi lo + lo hi on
+                           tcgen05 kind::f16, FP32 accumulate (about 16 significant bits) */
   CC_MIXED_TF32X3 = 3,  /* 3-pass TF32 split: x = hi + lo, a b ~ hi hi + hi lo + lo hi on tcgen05,
                            FP32 accumulate (about FP32 accuracy at a third of the TF32 rate) */
   CC_DF64 = 4           /* double-float: FP64 operands as FP32 pairs on the FP32 pipe (error-free

@@ -184,8 +184,8 @@ Engine& engine(cc_sys* sys) {
 }
 
 void check_prec(cc_precision p) {
-  CC_REQUIRE(p == CC_FP64 || p == CC_MIXED_TF32 || p == CC_MIXED_TF32X3 || p == CC_DF64, CC_ERR_INVALID,
-             "precision not available (CC_FP64, CC_MIXED_TF32, CC_MIXED_TF32X3 and CC_DF64 are)");
+  CC_REQUIRE(p == CC_FP64 || p == CC_MIXED_TF32 || p == CC_MIXED_TF32X3 || p == CC_MIXED_BF16X3 || p == CC_DF64, CC_ERR_INVALID,
+             "unknown precision");
 }
 
 // [t1 | t2] with t2 symmetrised: T2 only depends on t_ij^ab + t_ji^ba
@@ -217,7 +217,7 @@ void cc_solve_opts_default(cc_solve_opts* o, cc_method method, cc_precision prec
   o->level_shift = 0.0;
   o->diis_size = 8;
   o->jvp_fd = 0;
-  o->inner_rtol = prec == CC_MIXED_TF32 ? 1e-6 : prec == CC_MIXED_TF32X3 ? 1e-8 : 1e-12;
+  o->inner_rtol = prec == CC_MIXED_TF32 ? 1e-6 : prec == CC_MIXED_BF16X3 ? 1e-7 : prec == CC_MIXED_TF32X3 ? 1e-8 : 1e-12;
   o->inner_max = 50;
   o->af_direct = 0;
   o->verbose = 0;

@@ -116,20 +116,31 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
   double* Y = const_cast<double*>(Yv);
   double* Tm = const_cast<double*>(T);
   double* L = Y2_.val.p;
-  const char* tb = prec == CC_FP64 ? "ladder_build.fp64" : prec == CC_DF64 ? "ladder_build.df64" : "ladder_build.tf32";
+  const char* tb = prec == CC_FP64 ? "ladder_build.fp64"
+                   : prec == CC_DF64 ? "ladder_build.df64"
+                   : prec == CC_MIXED_BF16X3 ? "ladder_build.bf16" : "ladder_build.tf32";
   const char* tc = prec == CC_FP64 ? "ladder_contract.fp64"
-                                   : prec == CC_DF64 ? "ladder_contract.df64" : "ladder_contract.tf32";
-  const bool tensor = prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3;
-  // tensor cores: the slab goes straight from the first GEMM's epilogue, as TF32 segments in
-  // the K-major layout the second GEMM loads, to the second GEMM (no FP64 round trip)
-  const int nseg = prec == CC_MIXED_TF32X3 ? 3 : 1;
-  const long long kpad = ((long long)v * v + 31) / 32 * 32, kk = nseg * kpad;
+                   : prec == CC_DF64 ? "ladder_contract.df64"
+                   : prec == CC_MIXED_BF16X3 ? "ladder_contract.bf16" : "ladder_contract.tf32";
+  const bool tensor = prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3;
+  // tensor cores: the slab goes straight from the first GEMM's epilogue, as TF32 or BF16
+  // segments in the K-major layout the second GEMM loads, to the second GEMM (no FP64 round
+  // trip). A stage row is 128 bytes: k pads to 32 TF32 or 64 BF16 elements.
+  const bool bf = prec == CC_MIXED_BF16X3;
+  const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
+  const long long align = bf ? 64 : 32;
+  const long long kpad = ((long long)v * v + align - 1) / align * align, kk = nseg * kpad;
   const int rows_pad = (ladder_block_ * v + 255) / 256 * 256;
-  if (tensor && !W2_.p) {
-    W2_.alloc(ex_.pool, (size_t)rows_pad * 3 * kpad / 2 + 1);  // sized for three segments
-    CC_CUDA(cudaMemsetAsync(W2_.p, 0, W2_.n * sizeof(double), ex_.stream));  // zero k padding
+  if (tensor) {
+    const long long kmax = ((long long)v * v + 63) / 64 * 64;  // the larger of the two paddings
+    if (!W2_.p) W2_.alloc(ex_.pool, ((size_t)rows_pad * 3 * kmax * 4 + 7) / 8);
+    const int mode = (int)prec;
+    if (w2_mode_ != mode) {  // the k padding of this layout must read as zeros
+      CC_CUDA(cudaMemsetAsync(W2_.p, 0, W2_.n * sizeof(double), ex_.stream));
+      w2_mode_ = mode;
+    }
   }
-  float* W2 = reinterpret_cast<float*>(W2_.p);
+  void* W2 = W2_.p;
   for (int a0 = 0; a0 < v; a0 += ladder_block_) {
     const int al = std::min(ladder_block_, v - a0);
     const int bl = v - a0;  // b in [a0, v)

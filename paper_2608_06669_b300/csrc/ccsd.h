@@ -49,7 +49,8 @@ class Engine {
   Pair t_, u_, Btoo_, Btvv_, Btvo_, gam_, hY_, Ft_, Z_, Wk_, Woo_, Cint_, Dint_, Gv_, Go_, X_, Y2_;
   DBuf<double> W_;        // ladder workspace, ladder_block_ * v^3
   DBuf<double> XsYs_;     // stacked factors of the tangent ladder
-  DBuf<double> W2_;       // tensor-core ladder slab in staging layout (FP32 words)
+  DBuf<double> W2_;       // tensor-core ladder slab in staging layout (TF32 or BF16 words)
+  int w2_mode_ = -1;      // precision whose layout W2_ holds
   DBuf<double> scratch_;  // reduction partials
 };
 

@@ -132,16 +132,16 @@ struct CIdx {
   long long s0 = 0, s1 = 0, s2 = 0;
 };
 
-// Tensor-core operands kept in staging layout between two contractions: a K-major FP32
-// [rows][nseg * kpad] array whose nseg segments hold the TF32 high part or the low part.
-struct StagedOut {  // C written in that layout (C's strides count floats), beta must be 0
-  float* base;
+// Tensor-core operands kept in staging layout between two contractions: a K-major TF32 (FP32
+// words) or BF16 [rows][nseg * kpad] array whose nseg segments hold the high or the low part.
+struct StagedOut {  // C written in that layout (C's strides count elements), beta must be 0
+  void* base;
   long long kpad;
   int nseg, seg_lo;  // seg_lo: bit mask of the segments that hold the low part
 };
 struct StagedIn {  // the B operand already staged (rows padded to the tile, zero k padding)
-  const float* base;
-  int rows_pad, kk;  // kk = nseg * kpad floats per row
+  const void* base;
+  int rows_pad, kk;  // kk = nseg * kpad elements per row
 };
 
 struct GemmArgs {

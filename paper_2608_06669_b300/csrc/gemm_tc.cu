@@ -11,6 +11,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "common.h"
@@ -20,12 +22,27 @@ namespace {
 
 constexpr int TM = 128;         // tile rows = UMMA M
 constexpr int TN = 256;         // tile columns = UMMA N
-constexpr int TK = 32;          // k per pipeline stage: 32 FP32 = one 128-byte swizzle row
-constexpr int UK = 8;           // k per tcgen05.mma of kind::tf32
+// Operand element types: TF32 (kind::tf32, 32 per 128-byte row, 8 per MMA) and BF16
+// (kind::f16 with BF16 operands, 64 per row, 16 per MMA). A pipeline stage is 128 bytes of
+// k for every row in both cases, so the shared-memory layout does not depend on the type.
+template <bool BF>
+struct Elt;
+template <>
+struct Elt<false> {
+  using T = float;
+  static constexpr int TK = 32, UK = 8;
+  static constexpr uint32_t FMT = 2;  // TF32 in the instruction descriptor
+};
+template <>
+struct Elt<true> {
+  using T = __nv_bfloat16;
+  static constexpr int TK = 64, UK = 16;
+  static constexpr uint32_t FMT = 1;  // BF16
+};
 constexpr int STAGES = 4;
 constexpr int THREADS = 192;    // six warps: TMA producer, MMA issuer, four epilogue warps
-constexpr uint32_t A_BYTES = TM * TK * 4;
-constexpr uint32_t B_BYTES = TN * TK * 4;
+constexpr uint32_t A_BYTES = TM * 128;
+constexpr uint32_t B_BYTES = TN * 128;
 constexpr uint32_t TMEM_COLS = 2 * TN;  // two FP32 accumulators of TN columns (all 512)
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s bound on any wait
 
@@ -46,9 +63,18 @@ __device__ __forceinline__ float to_tf32(float x) {
 
 // writes x into the staging segments of one element: the TF32 high part, or the low part.
 // All in FP32: x - tf32(x) is exact in FP32, and nothing here touches the FP64 pipe.
-__device__ __forceinline__ void store_staged(float* p, long long kpad, int nseg, int seglo, float x) {
-  const float hi = to_tf32(x);
-  const float lo = to_tf32(__fsub_rn(x, hi));
+__device__ __forceinline__ void split(float x, float& hi, float& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(__fsub_rn(x, hi));
+}
+__device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(hi)));
+}
+template <typename T>
+__device__ __forceinline__ void store_staged(T* p, long long kpad, int nseg, int seglo, float x) {
+  T hi, lo;
+  split(x, hi, lo);
   for (int s = 0; s < nseg; ++s) p[(long long)s * kpad] = ((seglo >> s) & 1) ? lo : hi;
 }
 
@@ -57,8 +83,9 @@ __device__ __forceinline__ void store_staged(float* p, long long kpad, int nseg,
 // the low part lo = tf32(x - hi) instead of the high part hi = tf32(x); one segment with
 // mask 0 is the plain TF32 operand, three segments [hi|hi|lo] and [hi|lo|hi] on the two
 // operands give the three-pass split product hi hi + hi lo + lo hi along one long k.
+template <typename T>
 __global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
-                              int batch, int rows_pad, int k_pad, int nseg, int seg_lo, float* __restrict__ out) {
+                              int batch, int rows_pad, int k_pad, int nseg, int seg_lo, T* __restrict__ out) {
   const size_t tot = (size_t)batch * rows_pad * k_pad;
   const size_t row_len = (size_t)nseg * k_pad;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
@@ -66,20 +93,17 @@ __global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix
     size_t q = e / k_pad;
     int r = (int)(q % rows_pad);
     int b = (int)(q / rows_pad);
-    float hi = 0.0f, lo = 0.0f;
-    if (r < rows && k < K) {
-      double x = src[cidx(bix, b) + cidx(rix, r) + cidx(kix, k)];
-      hi = to_tf32((float)x);
-      lo = to_tf32((float)(x - (double)hi));
-    }
-    float* row = out + q * row_len + k;
+    T hi, lo;
+    split(r < rows && k < K ? (float)src[cidx(bix, b) + cidx(rix, r) + cidx(kix, k)] : 0.0f, hi, lo);
+    T* row = out + q * row_len + k;
     for (int s = 0; s < nseg; ++s) row[(size_t)s * k_pad] = ((seg_lo >> s) & 1) ? lo : hi;
   }
 }
 
 // split-k: C = alpha * sum_s part[s] + beta * C, the splits added in a fixed order (or, with
 // a staged output, alpha * sum written as TF32 segments)
-__global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int splits, float* Cs,
+template <typename T>
+__global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int splits, T* Cs,
                                         long long kpad, int nseg, int seglo) {
   const size_t tot = (size_t)g.batch * g.M * g.N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
@@ -120,7 +144,7 @@ struct TcArgs {
   double* C;
   float* part;  // split-k partial sums [splits][batch][M][N] (splits > 1)
   int* err;
-  float* Cs;    // non-null: C in staging layout (offsets from cm/cn/cb count floats)
+  void* Cs;     // non-null: C in staging layout (offsets from cm/cn/cb count elements)
   long long cs_kpad;
   int cs_nseg, cs_seglo;
 };
@@ -185,8 +209,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = TN, M = TM
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// instruction descriptor: D = F32, A = B = TF32 or BF16, both K-major, N = TN, M = TM
+template <bool BF>
+constexpr uint32_t idesc() {
+  return (1u << 4) | (Elt<BF>::FMT << 7) | (Elt<BF>::FMT << 10) | ((uint32_t)(TN >> 3) << 17) |
+         ((uint32_t)(TM >> 4) << 24);
+}
 
 // tile t -> (split, batch entry, first row, first column, k-block range)
 __device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int& bz, int& m0, int& n0, int& kb0,
@@ -212,8 +240,11 @@ constexpr size_t SMEM_BYTES = 1024 + SMEM_USED;
 //   warp 1: TMEM allocator and the single MMA-issuing thread; alternates two accumulators
 //   warps 2-5: epilogue (TMEM lane quadrant = warp % 4), releasing an accumulator as soon as
 //              it has been read, so the next tile's MMAs overlap this tile's stores
+template <bool BF>
 __global__ void __launch_bounds__(THREADS, 1)
-    gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
+  constexpr int TK = Elt<BF>::TK, UK = Elt<BF>::UK;
+  using T = typename Elt<BF>::T;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -288,12 +319,19 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
           for (int j = 0; j < TK / UK; ++j) {
-            const uint64_t da = sdesc(a0 + j * UK * 4), db = sdesc(b0 + j * UK * 4);
+            const uint64_t da = sdesc(a0 + j * 32), db = sdesc(b0 + j * 32);  // UK elements = 32 bytes
             const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                "l"(da), "l"(db), "r"(IDESC), "r"(accum)
-                : "memory");
+            if constexpr (BF) {
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "l"(da), "l"(db), "r"(idesc<BF>()), "r"(accum)
+                  : "memory");
+            } else {
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "l"(da), "l"(db), "r"(idesc<BF>()), "r"(accum)
+                  : "memory");
+            }
           }
           // frees the stage once these MMAs have read it
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
@@ -356,7 +394,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int rr = 0; rr < 32; ++rr) {
             const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
             if (ro >= 0 && n < g.N)
-              store_staged(g.Cs + ro + cn, g.cs_kpad, g.cs_nseg, g.cs_seglo, alpha_f * tile[rr * 33 + lane]);
+              store_staged(static_cast<T*>(g.Cs) + ro + cn, g.cs_kpad, g.cs_nseg, g.cs_seglo, alpha_f * tile[rr * 33 + lane]);
           }
         } else {
           const long long cn = n < g.N ? cidx(g.cn, n) : 0;
@@ -404,14 +442,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D map over a [batch][rows][k_pad] FP32 array, box = 32 (k) x box_rows x 1
-CUtensorMap make_map(const float* base, int k_pad, int rows_pad, int batch, int box_rows) {
+// 3-D map over a [batch][rows][k_pad] array of FP32 or BF16, box = 128 bytes of k x box_rows x 1
+CUtensorMap make_map(const void* base, int k_pad, int rows_pad, int batch, int box_rows, bool bf) {
   CUtensorMap m;
+  const cuuint64_t es = bf ? 2 : 4;
   cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)batch};
-  cuuint64_t strides[2] = {(cuuint64_t)k_pad * 4, (cuuint64_t)k_pad * rows_pad * 4};
-  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)k_pad * es, (cuuint64_t)k_pad * rows_pad * es};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
+  CUresult r = encode_fn()(&m, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                           const_cast<void*>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   CC_REQUIRE(r == CUDA_SUCCESS, CC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -420,48 +460,42 @@ CUtensorMap make_map(const float* base, int k_pad, int rows_pad, int batch, int 
 
 }  // namespace
 
-void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
-  CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3, CC_ERR_INVALID, "tensor-core precision not available");
-  CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
-  if (g.K <= 0) {
-    int blocks = (int)std::min<size_t>(((size_t)g.batch * g.M * g.N + 255) / 256, (size_t)ex.sm_count * 8);
-    scale_c_kernel<<<std::max(blocks, 1), 256, 0, ex.stream>>>(g);
-    ex.count();
-    CC_CUDA(cudaGetLastError());
-    return;
-  }
-  CC_REQUIRE((long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN) * g.batch < (1LL << 31), CC_ERR_INVALID,
-             "tensor-core contraction: too many tiles");
+namespace {
+
+template <bool BF>
+void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
+  using T = typename Elt<BF>::T;
+  constexpr int TK = Elt<BF>::TK;
   const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
   const int k_pad = (g.K + TK - 1) / TK * TK;
-  // the split precision stages [hi|hi|lo] against [hi|lo|hi] along a three times longer k
-  const int nseg = prec == CC_MIXED_TF32X3 ? 3 : 1;
+  // the split precisions stage [hi|hi|lo] against [hi|lo|hi] along a three times longer k
+  const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
   const int kk = nseg * k_pad;
   const size_t nA = (size_t)g.batch * rowsA * kk, nB = g.sb ? 0 : (size_t)g.batch * rowsB * kk;
-  DBuf<double> stA(ex.pool, (nA + 1) / 2), stB(ex.pool, (nB + 1) / 2);
-  float* fA = reinterpret_cast<float*>(stA.p);
-  float* fB = reinterpret_cast<float*>(stB.p);
+  DBuf<double> stA(ex.pool, (nA * sizeof(T) + 7) / 8), stB(ex.pool, (nB * sizeof(T) + 7) / 8);
+  T* fA = reinterpret_cast<T*>(stA.p);
+  T* fB = reinterpret_cast<T*>(stB.p);
   const size_t eA = (size_t)g.batch * rowsA * k_pad, eB = (size_t)g.batch * rowsB * k_pad;
   auto blocks_for = [&](size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)ex.sm_count * 16)); };
-  gather_kernel<<<blocks_for(eA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, nseg,
-                                                        nseg == 3 ? 0b100 : 0, fA);
+  gather_kernel<T><<<blocks_for(eA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, nseg,
+                                                           nseg == 3 ? 0b100 : 0, fA);
   ex.count();
   int rowsBmap = rowsB;
   if (g.sb) {
     // B was written in staging layout by an earlier contraction
     CC_REQUIRE(g.batch == 1 && g.sb->kk == kk && g.sb->rows_pad >= rowsB && g.sb->rows_pad % TN == 0,
                CC_ERR_INVALID, "staged operand does not match the contraction");
-    fB = const_cast<float*>(g.sb->base);
+    fB = static_cast<T*>(const_cast<void*>(g.sb->base));
     rowsBmap = g.sb->rows_pad;
   } else {
-    gather_kernel<<<blocks_for(eB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad, nseg,
-                                                          nseg == 3 ? 0b010 : 0, fB);
+    gather_kernel<T><<<blocks_for(eB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad,
+                                                             nseg, nseg == 3 ? 0b010 : 0, fB);
     ex.count();
   }
   CC_CUDA(cudaGetLastError());
   CC_REQUIRE(!g.so || g.beta == 0.0, CC_ERR_INVALID, "a staged output cannot accumulate");
-  CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM);
-  CUtensorMap mB = make_map(fB, kk, rowsBmap, g.batch, TN);
+  CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM, BF);
+  CUtensorMap mB = make_map(fB, kk, rowsBmap, g.batch, TN, BF);
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
@@ -499,23 +533,42 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   }
   static bool attr = false;
   if (!attr) {
-    CC_CUDA(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    CC_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     attr = true;
   }
   const int grid = std::min(a.tiles, ex.sm_count);  // persistent: at most one CTA per SM
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
-  gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
+  gemm_tc_kernel<BF><<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {
     const size_t tot = (size_t)g.batch * g.M * g.N;
-    tc_splitk_reduce_kernel<<<blocks_for(tot), 256, 0, ex.stream>>>(g, a.part, splits, a.Cs, a.cs_kpad, a.cs_nseg,
-                                                                     a.cs_seglo);
+    tc_splitk_reduce_kernel<T><<<blocks_for(tot), 256, 0, ex.stream>>>(g, a.part, splits, static_cast<T*>(a.Cs),
+                                                                        a.cs_kpad, a.cs_nseg, a.cs_seglo);
     ex.count();
     CC_CUDA(cudaGetLastError());
   }
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
+}
+
+}  // namespace
+
+void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
+  CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3, CC_ERR_INVALID,
+             "tensor-core precision not available");
+  CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
+  if (g.K <= 0) {
+    int blocks = (int)std::min<size_t>(((size_t)g.batch * g.M * g.N + 255) / 256, (size_t)ex.sm_count * 8);
+    scale_c_kernel<<<std::max(blocks, 1), 256, 0, ex.stream>>>(g);
+    ex.count();
+    CC_CUDA(cudaGetLastError());
+    return;
+  }
+  CC_REQUIRE((long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN) * g.batch < (1LL << 31), CC_ERR_INVALID,
+             "tensor-core contraction: too many tiles");
+  if (prec == CC_MIXED_BF16X3) run_tc<true>(ex, prec, g, tag);
+  else run_tc<false>(ex, prec, g, tag);
 }
 
 }  // namespace ccpnk

@@ -256,7 +256,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
   DBuf<double> red(ex.pool, 64 * 1024);
   double* scratch = red.p;
   double inner_rtol = opt.inner_rtol > 0 ? opt.inner_rtol
-                                         : (opt.prec == CC_MIXED_TF32 ? 1e-6 : opt.prec == CC_MIXED_TF32X3 ? 1e-8 : 1e-12);
+                                         : (opt.prec == CC_MIXED_TF32 ? 1e-6 : opt.prec == CC_MIXED_BF16X3 ? 1e-7 : opt.prec == CC_MIXED_TF32X3 ? 1e-8 : 1e-12);
   int inner_max = opt.inner_max > 0 ? opt.inner_max : 50;
   auto AFinv = [&](const double* b, double* x) {
     solve_AF(ex, s, b, x, opt.prec, inner_rtol, inner_max, opt.af_direct != 0, &st);
@@ -292,7 +292,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
   double energy = 0.0, rn = 0.0, rn_prev = 0.0, eta_prev = opt.eta_max;
   int status = CC_ERR_NOT_CONVERGED;
   // no point asking the linear solve for more than its operator's precision delivers
-  const double eta_min = opt.prec == CC_MIXED_TF32 ? 1e-4 : opt.prec == CC_MIXED_TF32X3 ? 1e-7 : 1e-10;
+  const double eta_min = opt.prec == CC_MIXED_TF32 ? 1e-4 : opt.prec == CC_MIXED_BF16X3 ? 1e-5 : opt.prec == CC_MIXED_TF32X3 ? 1e-7 : 1e-10;
   const int m_max = std::max(1, opt.m_max);
 
   if (opt.method == CC_FP_DIIS) {

@@ -84,6 +84,28 @@ def test_tf32x3_residual_and_jvp(ctx, o, v, naux, gauge):
     assert np.abs(j2 - p2).max() < 1e-6 * scale and np.abs(j1 - p1).max() < 1e-6 * scale
 
 
+@pytest.mark.parametrize("o,v,naux,gauge", [(2, 4, 5, "haar"), (5, 21, 13, "small"), (7, 33, 20, "haar")])
+def test_bf16x3_residual_and_jvp(ctx, o, v, naux, gauge):
+    """BF16 keeps 8 significant bits, so hi + lo holds 16 and each split product is off by
+    about 3 * 2^-18 relative; the bound is 2e-5 normwise."""
+    s = synth.make_system(o, v, naux, seed=11 + o, gauge=gauge)
+    rng = np.random.default_rng(5 * o + v)
+    t1, t2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    d1, d2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    g = gsys(ctx, s)
+    r1, r2, _ = g.residual(t1, t2, prec="bf16x3")
+    q1, q2, _ = cc.residual(s.fock, s.B, o, t1, t2)
+    scale = max(np.abs(q1).max(), np.abs(q2).max())
+    assert np.abs(r2 - q2).max() < 2e-5 * scale and np.abs(r1 - q1).max() < 2e-5 * scale
+    j1, j2 = g.jvp(t1, t2, d1, d2, prec="bf16x3")
+    p1, p2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+    scale = max(np.abs(p1).max(), np.abs(p2).max())
+    assert np.abs(j2 - p2).max() < 2e-5 * scale and np.abs(j1 - p1).max() < 2e-5 * scale
+    # and it is a real improvement over one TF32 pass
+    k1, k2 = g.jvp(t1, t2, d1, d2, prec="tf32")
+    assert np.abs(j2 - p2).max() < np.abs(k2 - p2).max()
+
+
 def test_tf32_jvp_workload_error(ctx):
     """The error of the TF32 JVP on the o=10, v=90 workload, stated against the FP64 oracle."""
     s = synth.workload("o10v90_rotated")
@@ -96,7 +118,7 @@ def test_tf32_jvp_workload_error(ctx):
     assert err < TF32_TOL
 
 
-@pytest.mark.parametrize("method,prec", [("pnk", "tf32"), ("nk", "tf32"), ("pnk", "tf32x3")])
+@pytest.mark.parametrize("method,prec", [("pnk", "tf32"), ("nk", "tf32"), ("pnk", "tf32x3"), ("pnk", "bf16x3")])
 def test_mixed_solve_reaches_fp64_root(ctx, method, prec):
     s = synth.workload("o5v20_canonical")
     ref = json.load(open(GOLDEN))["o5v20_canonical"]["e_corr"]
