@@ -59,6 +59,12 @@ void system_init(const Exec& ex, System& s, int o, int v, int P, const double* f
   k_make_L_ovov(ex, o, v, s.Govov.p, s.Lovov.p);
 }
 
+int ladder_block_for(int v) {
+  const double cap = 2.0 * 1024 * 1024 * 1024;
+  const double per_a = 8.0 * (double)v * v * v;
+  return std::max(1, std::min((v + 7) / 8, (int)(cap / std::max(per_a, 1.0))));
+}
+
 Engine::Engine(const Exec& ex, const System& s) : ex_(ex), s_(s) {
   const int o = s.o, v = s.v, n = s.n, P = s.P;
   const size_t oovv = (size_t)o * o * v * v;
@@ -79,11 +85,7 @@ Engine::Engine(const Exec& ex, const System& s) : ex_(ex), s_(s) {
   alloc(Go_, (size_t)o * o);
   alloc(X_, oovv);
   alloc(Y2_, oovv);
-  // ladder workspace: blocks of about v/8 values of a (so the half-triangle saving applies),
-  // with an (a, b, c, d) slab of at most ~512 MB
-  const double cap = 512.0 * 1024 * 1024;
-  const double per_a = 8.0 * (double)v * v * v;
-  ladder_block_ = std::max(1, std::min((v + 7) / 8, (int)(cap / std::max(per_a, 1.0))));
+  ladder_block_ = ladder_block_for(v);
   W_.alloc(ex.pool, (size_t)ladder_block_ * v * v * v);
   // the tangent's stacked factors [dBt_vv ; Bt_vv] and [Bt_vv ; dBt_vv]
   XsYs_.alloc(ex.pool, 4 * (size_t)P * v * v);

@@ -23,6 +23,10 @@ struct System {
 
 void system_init(const Exec& ex, System& s, int o, int v, int P, const double* fock_dev, const double* B_dev);
 
+// Values of a per ladder block: about v/8 (so the half-triangle saving applies) with an FP64
+// (a, b, c, d) slab of at most 2 GiB; larger blocks give the tensor-core GEMMs more tiles.
+int ladder_block_for(int v);
+
 // Intermediates of one residual evaluation; the tangent program reuses the values.
 class Engine {
  public:

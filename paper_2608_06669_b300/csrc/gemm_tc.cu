@@ -40,7 +40,8 @@ struct Elt<true> {
   static constexpr uint32_t FMT = 1;  // BF16
 };
 constexpr int STAGES = 4;
-constexpr int THREADS = 192;    // six warps: TMA producer, MMA issuer, four epilogue warps
+constexpr int EPI_WARPS = 8;    // two per TMEM lane quadrant, each on half of the tile's columns
+constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA producer, MMA issuer, epilogue warps
 constexpr uint32_t A_BYTES = TM * 128;
 constexpr uint32_t B_BYTES = TN * 128;
 constexpr uint32_t TMEM_COLS = 2 * TN;  // two FP32 accumulators of TN columns (all 512)
@@ -70,6 +71,17 @@ __device__ __forceinline__ void split(float x, float& hi, float& lo) {
 __device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(hi)));
+}
+// the epilogue's fixed-layout versions: one segment (hi), or three as [hi|lo|hi]
+template <int NSEG, typename T>
+__device__ __forceinline__ void store_staged_fixed(T* p, long long kpad, float x) {
+  T hi, lo;
+  split(x, hi, lo);
+  p[0] = hi;
+  if constexpr (NSEG == 3) {
+    p[kpad] = lo;
+    p[2 * kpad] = hi;
+  }
 }
 template <typename T>
 __device__ __forceinline__ void store_staged(T* p, long long kpad, int nseg, int seglo, float x) {
@@ -137,6 +149,7 @@ __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
 
 struct TcArgs {
   int M, N, kblocks, num_m, num_n, tiles;  // tiles counts splits x batch x num_m x num_n
+  int m_fast;                             // 1: consecutive tiles walk down m (they share a B tile)
   int splits, kchunk;                     // split-k: k blocks [s * kchunk, (s + 1) * kchunk)
   int batch;
   CIdx cm, cn, cb;
@@ -224,23 +237,35 @@ __device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int
   sp = outer / g.batch;
   bz = outer - sp * g.batch;
   const int r = t - outer * per;
-  m0 = (r / g.num_n) * TM;
-  n0 = (r % g.num_n) * TN;
+  if (g.m_fast) {
+    m0 = (r % g.num_m) * TM;
+    n0 = (r / g.num_m) * TN;
+  } else {
+    m0 = (r / g.num_n) * TM;
+    n0 = (r % g.num_n) * TN;
+  }
   kb0 = sp * g.kchunk;
   kb1 = min(g.kblocks, kb0 + g.kchunk);
 }
 
 // shared memory: STAGES x (A tile, B tile), the epilogue's turn-around tiles, barriers
 constexpr uint32_t EP_FLOATS = 32 * 33;
-constexpr size_t SMEM_USED = (size_t)STAGES * (A_BYTES + B_BYTES) + 4 * EP_FLOATS * 4 + (2 * STAGES + 4) * 8 + 16;
+constexpr size_t SMEM_USED =
+    (size_t)STAGES * (A_BYTES + B_BYTES) + EPI_WARPS * EP_FLOATS * 4 + (2 * STAGES + 4) * 8 + 16;
+static_assert(1024 + SMEM_USED <= 232448, "shared memory beyond 227 KB");
+
+// What the epilogue writes: C in FP64 (alpha acc + beta C), split-k FP32 partial sums, or the
+// staging layout of a later contraction with one segment or three ([hi|lo|hi]).
+enum { EPI_F64 = 0, EPI_PART = 1, EPI_STAGED1 = 2, EPI_STAGED3 = 3 };
 constexpr size_t SMEM_BYTES = 1024 + SMEM_USED;
 
 // Persistent, warp-specialised GEMM: each CTA walks tiles blockIdx.x, +gridDim.x, ...
 //   warp 0: TMA producer through the STAGES-deep full/empty ring
 //   warp 1: TMEM allocator and the single MMA-issuing thread; alternates two accumulators
-//   warps 2-5: epilogue (TMEM lane quadrant = warp % 4), releasing an accumulator as soon as
-//              it has been read, so the next tile's MMAs overlap this tile's stores
-template <bool BF>
+//   warps 2-9: epilogue (TMEM lane quadrant = warp % 4, two warps per quadrant on the two
+//              column halves), releasing an accumulator as soon as it has been read, so the
+//              next tile's MMAs overlap this tile's stores
+template <bool BF, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
   constexpr int TK = Elt<BF>::TK, UK = Elt<BF>::UK;
@@ -250,7 +275,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   float* ep = reinterpret_cast<float*>(sB + STAGES * B_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ep + 4 * EP_FLOATS);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ep + EPI_WARPS * EP_FLOATS);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
   const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
@@ -263,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
-      mbar_init(tempty0 + 8 * a, 4);  // one arrival per epilogue warp
+      mbar_init(tempty0 + 8 * a, EPI_WARPS);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -345,7 +370,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncwarp();
   } else {
-    const int quad = warp & 3;  // the TMEM lanes (tile rows) this warp may read
+    const int quad = warp & 3;          // the TMEM lanes (tile rows) this warp may read
+    const int half = (warp - 2) >> 2;   // the half of the tile's columns it stores
     const float alpha_f = (float)g.alpha;
     float* tile = ep + (warp - 2) * EP_FLOATS;
     int it = 0;
@@ -362,10 +388,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int my_row = m0 + quad * 32 + lane;
       long long my_off = -1;
       if (my_row < g.M)
-        my_off = g.splits > 1 ? (((long long)sp * g.batch + bz) * g.M + my_row) * (long long)g.N
-                              : cidx(g.cb, bz) + cidx(g.cm, my_row);
+        my_off = EPI == EPI_PART ? (((long long)sp * g.batch + bz) * g.M + my_row) * (long long)g.N
+                                 : cidx(g.cb, bz) + cidx(g.cm, my_row);
 #pragma unroll 1
-      for (int c0 = 0; c0 < TN; c0 += 32) {
+      for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 32) {
         uint32_t r[32];
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TN + c0);
         asm volatile(
@@ -382,36 +408,35 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         // a warp's stores run along a row of C
         const int n = n0 + c0 + lane;
-        if (g.splits > 1) {
+        const bool n_ok = n < g.N;
+        if constexpr (EPI == EPI_PART) {
 #pragma unroll 8
           for (int rr = 0; rr < 32; ++rr) {
             const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
-            if (ro >= 0 && n < g.N) g.part[ro + n] = tile[rr * 33 + lane];
+            if (ro >= 0 && n_ok) g.part[ro + n] = tile[rr * 33 + lane];
           }
-        } else if (g.Cs) {
-          const long long cn = n < g.N ? cidx(g.cn, n) : 0;
-#pragma unroll 4
+        } else if constexpr (EPI == EPI_STAGED1 || EPI == EPI_STAGED3) {
+          T* cs = static_cast<T*>(g.Cs) + (n_ok ? cidx(g.cn, n) : 0);
+          const long long kpad = g.cs_kpad;
+#pragma unroll 8
           for (int rr = 0; rr < 32; ++rr) {
             const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
-            if (ro >= 0 && n < g.N)
-              store_staged(static_cast<T*>(g.Cs) + ro + cn, g.cs_kpad, g.cs_nseg, g.cs_seglo, alpha_f * tile[rr * 33 + lane]);
+            if (ro >= 0 && n_ok)
+              store_staged_fixed<EPI == EPI_STAGED3 ? 3 : 1>(cs + ro, kpad, alpha_f * tile[rr * 33 + lane]);
           }
         } else {
-          const long long cn = n < g.N ? cidx(g.cn, n) : 0;
+          double* cc = g.C + (n_ok ? cidx(g.cn, n) : 0);
           if (g.beta == 0.0) {
 #pragma unroll 8
             for (int rr = 0; rr < 32; ++rr) {
               const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
-              if (ro >= 0 && n < g.N) g.C[ro + cn] = g.alpha * (double)tile[rr * 33 + lane];
+              if (ro >= 0 && n_ok) cc[ro] = g.alpha * (double)tile[rr * 33 + lane];
             }
           } else {
 #pragma unroll 8
             for (int rr = 0; rr < 32; ++rr) {
               const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
-              if (ro >= 0 && n < g.N) {
-                double* c = g.C + ro + cn;
-                *c = fma(g.beta, *c, g.alpha * (double)tile[rr * 33 + lane]);
-              }
+              if (ro >= 0 && n_ok) cc[ro] = fma(g.beta, cc[ro], g.alpha * (double)tile[rr * 33 + lane]);
             }
           }
         }
@@ -503,12 +528,27 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   a.num_m = rowsA / TM;
   a.num_n = rowsB / TN;
   a.batch = g.batch;
+  // Tiles that run at the same time share operand tiles through L2: the shorter of the two
+  // tile dimensions runs fastest, so a wave of CTAs covers whole columns (or rows) of tiles
+  // and the long operand is read from HBM about once instead of once per tile row.
+  a.m_fast = a.num_m <= a.num_n ? 1 : 0;
   // split k when the output has fewer tiles than SMs and the sum is long: every split is a
-  // tile of its own that writes FP32 partial sums, added in order by a second kernel
+  // tile of its own that writes FP32 partial sums, added in order by a second kernel. The
+  // factor minimises the waves of the persistent grid per unit of work, ceil(tiles s / SMs) / s
+  // (ties to the smaller factor), so the last wave is not left mostly idle.
   const long long base_tiles = (long long)a.num_m * a.num_n * g.batch;
   int splits = 1;
-  if (base_tiles < ex.sm_count && a.kblocks >= 8)
-    splits = (int)std::max<long long>(1, std::min<long long>((ex.sm_count + base_tiles - 1) / base_tiles, a.kblocks / 4));
+  if (base_tiles < ex.sm_count && a.kblocks >= 8) {
+    const int smax = (int)std::min<long long>(16, a.kblocks / 4);
+    double best = 1.0;
+    for (int sp = 2; sp <= smax; ++sp) {
+      const double waves = (double)((base_tiles * sp + ex.sm_count - 1) / ex.sm_count);
+      if (waves / sp < best - 1e-9) {
+        best = waves / sp;
+        splits = sp;
+      }
+    }
+  }
   a.kchunk = (a.kblocks + splits - 1) / splits;
   splits = (a.kblocks + a.kchunk - 1) / a.kchunk;  // no empty split
   a.splits = splits;
@@ -531,15 +571,30 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
     part.alloc(ex.pool, (np + 1) / 2);
     a.part = reinterpret_cast<float*>(part.p);
   }
-  static bool attr = false;
-  if (!attr) {
-    CC_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    attr = true;
+  // the epilogue's output mode is a template parameter, so its store loop has no run-time
+  // branching on the layout
+  int epi = EPI_F64;
+  if (splits > 1) {
+    epi = EPI_PART;
+  } else if (g.so) {
+    CC_REQUIRE((g.so->nseg == 1 && g.so->seg_lo == 0) || (g.so->nseg == 3 && g.so->seg_lo == 0b010), CC_ERR_INVALID,
+               "staged output layout not supported by the tensor-core epilogue");
+    epi = g.so->nseg == 3 ? EPI_STAGED3 : EPI_STAGED1;
+  }
+  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
+      epi == EPI_PART      ? gemm_tc_kernel<BF, EPI_PART>
+      : epi == EPI_STAGED1 ? gemm_tc_kernel<BF, EPI_STAGED1>
+      : epi == EPI_STAGED3 ? gemm_tc_kernel<BF, EPI_STAGED3>
+                           : gemm_tc_kernel<BF, EPI_F64>;
+  static bool attr[4] = {false, false, false, false};
+  if (!attr[epi]) {
+    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    attr[epi] = true;
   }
   const int grid = std::min(a.tiles, ex.sm_count);  // persistent: at most one CTA per SM
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
-  gemm_tc_kernel<BF><<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
+  kern<<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {

@@ -5,6 +5,7 @@
 // what else runs.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -40,12 +41,13 @@ struct Request {
 size_t footprint_bytes(int o, int v, int naux, const cc_solve_opts& op) {
   const double n = o + v, ov = (double)o * v, oovv = ov * ov;
   const double namp = ov + oovv;
-  const double per_a = 8.0 * (double)v * v * v;
-  const double lb = std::max(1.0, std::min((double)v, 512.0 * 1024 * 1024 / std::max(per_a, 1.0)));
+  const double lb = ccpnk::ladder_block_for(v);
   double doubles = 0;
   doubles += 3.0 * naux * n * n;                            // B (upload, blocks)
   doubles += 36.0 * oovv + 8.0 * naux * n * n;              // engine values + tangents
   doubles += lb * v * v * v;                                // ladder slab
+  if (op.prec != CC_FP64 && op.prec != CC_DF64)             // its tensor-core staging copy
+    doubles += std::ceil(lb * v / 256.0) * 256.0 * 3.0 * std::ceil((double)v * v / 64.0) * 64.0 / 2.0;
   doubles += (op.m_max + 8.0) * namp;                       // outer Krylov basis and vectors
   doubles += (op.af_direct ? 2.0 : (op.inner_max + 2.0)) * namp;  // A_F inverse work
   doubles += 4.0 * oovv;                                    // split-k partials, staging

@@ -197,7 +197,7 @@ def test_invalid_inputs_are_rejected(ctx):
         ccpnk.System(ctx, 0, 3, 2, s.fock, s.B)
     g = gpu_system(ctx, s)
     with pytest.raises(ccpnk.CCError):
-        g.residual(np.zeros((2, 3)), np.zeros((2, 2, 3, 3)), prec=2)
+        g.residual(np.zeros((2, 3)), np.zeros((2, 2, 3, 3)), prec=9)
 
 
 def _golden():
