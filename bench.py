@@ -419,8 +419,46 @@ def run_kernels(args):
                           **extra, **{k: rep[k] for k in keep}}), flush=True)
 
 
+def run_case(args):
+    """One residual or JVP evaluation on a named workload or an (o, v, naux) system: the small,
+    single-call cases that kernel profiles are taken on."""
+    import torch
+
+    from paper_2608_06669_b300 import ccpnk, synth
+
+    import numpy as np
+
+    spec = args.case
+    if "," in spec:
+        o, v, P = (int(x) for x in spec.split(","))
+        s = synth.make_system(o, v, P, seed=4, gauge="small")
+    else:
+        s = synth.workload(spec)
+    o, v = s.o, s.v
+    ctx = ccpnk.Context(0)
+    g = ccpnk.System.from_synth(ctx, s)
+    t1, t2 = synth.random_amplitudes(np.random.default_rng(0), o, v, 0.02, 0.02)
+    T1, T2 = torch.from_numpy(t1).cuda(), torch.from_numpy(t2).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if args.case_op == "jvp":
+        _, out = g.jvp(T1, T2, T1, T2, prec=args.case_prec)
+    else:
+        _, out, _ = g.residual(T1, T2, prec=args.case_prec)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"mode": "case", "case": spec, "op": args.case_op, "prec": args.case_prec, "o": o, "v": v,
+                      "naux": s.naux, "seconds": dt, "max_abs": float(out.abs().max()),
+                      "device_bytes": ctx.device_bytes}), flush=True)
+    g.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="", help="one evaluation on a workload name or 'o,v,naux' instead")
+    ap.add_argument("--case-op", default="jvp", choices=["jvp", "residual"])
+    ap.add_argument("--case-prec", default="tf32x3", choices=["fp64", "tf32", "tf32x3", "bf16x3", "df64"])
     ap.add_argument("--kernels", default="", help="per-kernel rates and capped solves on this workload instead")
     ap.add_argument("--shift", type=float, default=0.2, help="FP+DIIS level shift in --kernels")
     ap.add_argument("--no-fp64-solve", action="store_true")
@@ -443,6 +481,8 @@ def main():
         run_serve(args)
     elif args.kernels:
         run_kernels(args)
+    elif args.case:
+        run_case(args)
     else:
         run_ours(args)
 

@@ -18,6 +18,7 @@ struct System {
   bool eig_ready = false;
   std::vector<double> eo, ev;
   DBuf<double> Uo, Uv;  // column eigenvectors, o x o and v x v
+  DBuf<double> eig_d;   // [eo | ev] on the device
   size_t namp() const { return (size_t)o * v + (size_t)o * o * v * v; }
 };
 
@@ -60,7 +61,9 @@ class Engine {
 
 // y = A_F x on [x1 | x2] vectors (Eq. Preconditioner, App. C)
 void apply_AF(const Exec& ex, const System& s, const double* x, double* y, cc_precision prec);
-// y = (A_F + shift)^{-1} x in the eigenbases of the Fock blocks (exact Sylvester inverse)
-void solve_AF_direct(const Exec& ex, System& s, const double* x, double* y, double shift, double* work);
+// y = (A_F + shift)^{-1} x in the eigenbases of the Fock blocks (exact Sylvester inverse); the
+// four basis rotations run at prec, the division by the eigenvalue differences in FP64
+void solve_AF_direct(const Exec& ex, System& s, const double* x, double* y, double shift, double* work,
+                     cc_precision prec = CC_FP64);
 
 }  // namespace ccpnk

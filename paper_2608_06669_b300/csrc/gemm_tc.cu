@@ -90,47 +90,118 @@ __device__ __forceinline__ void store_staged(T* p, long long kpad, int nseg, int
   for (int s = 0; s < nseg; ++s) p[(long long)s * kpad] = ((seglo >> s) & 1) ? lo : hi;
 }
 
+// Offsets of a compound index walked in steps of a fixed size: the mixed-radix digits are
+// carried forward instead of divided out for every element (a division only on a carry).
+struct CWalk {
+  long long off;
+  int i0, i1, i2;
+  __device__ __forceinline__ void init(const CIdx& c, int x) {
+    if (c.e1 == 1 && c.e2 == 1) {
+      i0 = x;
+      i1 = i2 = 0;
+    } else {
+      i2 = x % c.e2;
+      const int r = x / c.e2;
+      i1 = r % c.e1;
+      i0 = r / c.e1;
+    }
+    off = (long long)i0 * c.s0 + (long long)i1 * c.s1 + (long long)i2 * c.s2;
+  }
+  __device__ __forceinline__ void step(const CIdx& c, int d) {
+    if (c.e1 == 1 && c.e2 == 1) {
+      i0 += d;
+      off += (long long)d * c.s0;
+      return;
+    }
+    i2 += d;
+    if (i2 >= c.e2) {
+      const int q = i2 / c.e2;
+      i2 -= q * c.e2;
+      i1 += q;
+      if (i1 >= c.e1) {
+        const int q1 = i1 / c.e1;
+        i1 -= q1 * c.e1;
+        i0 += q1;
+      }
+    }
+    off = (long long)i0 * c.s0 + (long long)i1 * c.s1 + (long long)i2 * c.s2;
+  }
+};
+
+// The warp-per-row kernels below cut a row into pieces of ROW_PIECE elements, so that short
+// and long rows alike give enough warps to fill the GPU.
+constexpr int ROW_PIECE = 256;
+
 // out[b][r][s * k_pad + k] for r < rows_pad, k < k_pad and the nseg segments s of a row
-// (FP32, TF32-rounded, zero outside rows x K). seg_lo is a bit mask of the segments that hold
-// the low part lo = tf32(x - hi) instead of the high part hi = tf32(x); one segment with
-// mask 0 is the plain TF32 operand, three segments [hi|hi|lo] and [hi|lo|hi] on the two
-// operands give the three-pass split product hi hi + hi lo + lo hi along one long k.
+// (TF32 words or BF16, zero outside rows x K). seg_lo is a bit mask of the segments that hold
+// the low part lo = x - hi instead of the high part hi; one segment with mask 0 is the plain
+// operand, three segments [hi|hi|lo] and [hi|lo|hi] on the two operands give the three-pass
+// split product hi hi + hi lo + lo hi along one long k. One warp per piece of a staged row:
+// the row's source offset is located once, and the lanes walk k.
 template <typename T>
 __global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
                               int batch, int rows_pad, int k_pad, int nseg, int seg_lo, T* __restrict__ out) {
-  const size_t tot = (size_t)batch * rows_pad * k_pad;
+  const int lane = threadIdx.x & 31;
+  const int pieces = (k_pad + ROW_PIECE - 1) / ROW_PIECE;
+  const long long items = (long long)batch * rows_pad * pieces;
   const size_t row_len = (size_t)nseg * k_pad;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    int k = (int)(e % k_pad);
-    size_t q = e / k_pad;
-    int r = (int)(q % rows_pad);
-    int b = (int)(q / rows_pad);
-    T hi, lo;
-    split(r < rows && k < K ? (float)src[cidx(bix, b) + cidx(rix, r) + cidx(kix, k)] : 0.0f, hi, lo);
-    T* row = out + q * row_len + k;
-    for (int s = 0; s < nseg; ++s) row[(size_t)s * k_pad] = ((seg_lo >> s) & 1) ? lo : hi;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = w0; it < items; it += nw) {
+    const long long q = it / pieces;  // staged row b * rows_pad + r
+    const int k0 = (int)(it - q * pieces) * ROW_PIECE, k1 = min(k_pad, k0 + ROW_PIECE);
+    const int b = (int)(q / rows_pad), r = (int)(q - (long long)b * rows_pad);
+    T* row = out + (size_t)q * row_len;
+    if (r >= rows) {
+      T z, zl;
+      split(0.0f, z, zl);
+      for (int k = k0 + lane; k < k1; k += 32)
+        for (int s = 0; s < nseg; ++s) row[(size_t)s * k_pad + k] = z;
+      continue;
+    }
+    const double* srow = src + cidx(bix, b) + cidx(rix, r);
+    CWalk kw;
+    kw.init(kix, k0 + lane);
+    for (int k = k0 + lane; k < k1; k += 32) {
+      T hi, lo;
+      split(k < K ? (float)srow[kw.off] : 0.0f, hi, lo);
+      for (int s = 0; s < nseg; ++s) row[(size_t)s * k_pad + k] = ((seg_lo >> s) & 1) ? lo : hi;
+      kw.step(kix, 32);
+    }
   }
 }
 
 // split-k: C = alpha * sum_s part[s] + beta * C, the splits added in a fixed order (or, with
-// a staged output, alpha * sum written as TF32 segments)
+// a staged output, alpha * sum written as TF32 or BF16 segments). One warp per piece of an
+// output row.
 template <typename T>
 __global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int splits, T* Cs,
                                         long long kpad, int nseg, int seglo) {
+  const int lane = threadIdx.x & 31;
   const size_t tot = (size_t)g.batch * g.M * g.N;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    int n = (int)(e % g.N);
-    size_t r = e / g.N;
-    int m = (int)(r % g.M);
-    int b = (int)(r / g.M);
-    double s = 0.0;
-    for (int q = 0; q < splits; ++q) s += (double)part[(size_t)q * tot + e];
-    const long long off = cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
-    if (Cs) {
-      store_staged(Cs + off, kpad, nseg, seglo, (float)(g.alpha * s));
-    } else {
-      double* c = g.C + off;
-      *c = g.beta == 0.0 ? g.alpha * s : fma(g.beta, *c, g.alpha * s);
+  const int pieces = (g.N + ROW_PIECE - 1) / ROW_PIECE;
+  const long long items = (long long)g.batch * g.M * pieces;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = w0; it < items; it += nw) {
+    const long long q = it / pieces;  // output row b * M + m
+    const int n0 = (int)(it - q * pieces) * ROW_PIECE, n1 = min(g.N, n0 + ROW_PIECE);
+    const int b = (int)(q / g.M), m = (int)(q - (long long)b * g.M);
+    const long long rowoff = cidx(g.cb, b) + cidx(g.cm, m);
+    const float* pr = part + (size_t)q * g.N;
+    CWalk cw;
+    cw.init(g.cn, n0 + lane);
+    for (int n = n0 + lane; n < n1; n += 32) {
+      double s = 0.0;
+      for (int p = 0; p < splits; ++p) s += (double)pr[(size_t)p * tot + n];
+      const long long off = rowoff + cw.off;
+      if (Cs) {
+        store_staged(Cs + off, kpad, nseg, seglo, (float)(g.alpha * s));
+      } else {
+        double* c = g.C + off;
+        *c = g.beta == 0.0 ? g.alpha * s : fma(g.beta, *c, g.alpha * s);
+      }
+      cw.step(g.cn, 32);
     }
   }
 }
@@ -500,9 +571,12 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   DBuf<double> stA(ex.pool, (nA * sizeof(T) + 7) / 8), stB(ex.pool, (nB * sizeof(T) + 7) / 8);
   T* fA = reinterpret_cast<T*>(stA.p);
   T* fB = reinterpret_cast<T*>(stB.p);
-  const size_t eA = (size_t)g.batch * rowsA * k_pad, eB = (size_t)g.batch * rowsB * k_pad;
-  auto blocks_for = [&](size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)ex.sm_count * 16)); };
-  gather_kernel<T><<<blocks_for(eA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, nseg,
+  // warp-per-row-piece kernels: eight pieces per 256-thread block and pass
+  auto blocks_for_rows = [&](size_t rows, size_t row_len) {
+    const size_t items = rows * ((row_len + ROW_PIECE - 1) / ROW_PIECE);
+    return (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
+  };
+  gather_kernel<T><<<blocks_for_rows((size_t)g.batch * rowsA, k_pad), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, nseg,
                                                            nseg == 3 ? 0b100 : 0, fA);
   ex.count();
   int rowsBmap = rowsB;
@@ -513,7 +587,7 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
     fB = static_cast<T*>(const_cast<void*>(g.sb->base));
     rowsBmap = g.sb->rows_pad;
   } else {
-    gather_kernel<T><<<blocks_for(eB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad,
+    gather_kernel<T><<<blocks_for_rows((size_t)g.batch * rowsB, k_pad), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad,
                                                              nseg, nseg == 3 ? 0b010 : 0, fB);
     ex.count();
   }
@@ -598,8 +672,7 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {
-    const size_t tot = (size_t)g.batch * g.M * g.N;
-    tc_splitk_reduce_kernel<T><<<blocks_for(tot), 256, 0, ex.stream>>>(g, a.part, splits, static_cast<T*>(a.Cs),
+    tc_splitk_reduce_kernel<T><<<blocks_for_rows((size_t)g.batch * g.M, g.N), 256, 0, ex.stream>>>(g, a.part, splits, static_cast<T*>(a.Cs),
                                                                         a.cs_kpad, a.cs_nseg, a.cs_seglo);
     ex.count();
     CC_CUDA(cudaGetLastError());

@@ -159,6 +159,10 @@ void ensure_eig(const Exec& ex, System& s) {
   s.Uv.alloc(ex.pool, (size_t)v * v);
   CC_CUDA(cudaMemcpyAsync(s.Uo.p, Vo.data(), Vo.size() * sizeof(double), cudaMemcpyHostToDevice, ex.stream));
   CC_CUDA(cudaMemcpyAsync(s.Uv.p, Vv.data(), Vv.size() * sizeof(double), cudaMemcpyHostToDevice, ex.stream));
+  std::vector<double> e(s.eo);
+  e.insert(e.end(), s.ev.begin(), s.ev.end());
+  s.eig_d.alloc(ex.pool, e.size());
+  CC_CUDA(cudaMemcpyAsync(s.eig_d.p, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice, ex.stream));
   CC_CUDA(cudaStreamSynchronize(ex.stream));
   s.eig_ready = true;
 }
@@ -186,40 +190,44 @@ __global__ void eig_divide_kernel(int o, int v, const double* __restrict__ eo, c
 
 // x = (A_F + shift)^{-1} b: A_F is a sum of commuting Kronecker terms of the occupied and
 // virtual Fock blocks, so it is diagonal in their eigenbases.
-void solve_AF_direct(const Exec& ex, System& s, const double* bin, double* x, double shift, double* work) {
+void solve_AF_direct(const Exec& ex, System& s, const double* bin, double* x, double shift, double* work,
+                     cc_precision prec) {
   ensure_eig(ex, s);
   const int o = s.o, v = s.v;
   const size_t ov = (size_t)o * v;
   double* b = const_cast<double*>(bin);
   auto Uo = [&](const char* l) { return view(s.Uo.p, l, {o, o}); };
   auto Uv = [&](const char* l) { return view(s.Uv.p, l, {v, v}); };
-  const cc_precision P64 = CC_FP64;
+  const cc_precision rp = prec;
   // rotate in: c = Uo^T b Uv (singles), Uo^T Uo^T b Uv Uv (doubles)
   double* w1 = work;
   double* w2 = work + s.namp();
-  contract(ex, P64, 1.0, view(b, "kc", {o, v}), Uv("ca"), 0.0, view(w1, "ka", {o, v}));
-  contract(ex, P64, 1.0, Uo("ki"), view(w1, "ka", {o, v}), 0.0, view(x, "ia", {o, v}));
-  contract(ex, P64, 1.0, view(b + ov, "klcd", {o, o, v, v}), Uv("db"), 0.0, view(w2, "klcb", {o, o, v, v}));
-  contract(ex, P64, 1.0, Uv("ca"), view(w2, "klcb", {o, o, v, v}), 0.0, view(w1 + ov, "klab", {o, o, v, v}));
-  contract(ex, P64, 1.0, view(w1 + ov, "klab", {o, o, v, v}), Uo("lj"), 0.0, view(w2, "kjab", {o, o, v, v}));
-  contract(ex, P64, 1.0, Uo("ki"), view(w2, "kjab", {o, o, v, v}), 0.0, view(x + ov, "ijab", {o, o, v, v}));
+  contract(ex, rp, 1.0, view(b, "kc", {o, v}), Uv("ca"), 0.0, view(w1, "ka", {o, v}));
+  contract(ex, rp, 1.0, Uo("ki"), view(w1, "ka", {o, v}), 0.0, view(x, "ia", {o, v}));
+  contract(ex, rp, 1.0, view(b + ov, "klcd", {o, o, v, v}), Uv("db"), 0.0, view(w2, "klcb", {o, o, v, v}));
+  contract(ex, rp, 1.0, Uv("ca"), view(w2, "klcb", {o, o, v, v}), 0.0, view(w1 + ov, "klab", {o, o, v, v}));
+  contract(ex, rp, 1.0, view(w1 + ov, "klab", {o, o, v, v}), Uo("lj"), 0.0, view(w2, "kjab", {o, o, v, v}));
+  contract(ex, rp, 1.0, Uo("ki"), view(w2, "kjab", {o, o, v, v}), 0.0, view(x + ov, "ijab", {o, o, v, v}));
   // divide by the eigenvalue differences
-  std::vector<double> e(s.eo);
-  e.insert(e.end(), s.ev.begin(), s.ev.end());
-  double* ed = w2;  // small, reused before the back rotation writes w2
-  CC_CUDA(cudaMemcpyAsync(ed, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice, ex.stream));
+  const double* ed = s.eig_d.p;
   int blocks = std::min<size_t>((s.namp() + 255) / 256, (size_t)ex.sm_count * 8);
   eig_divide_kernel<<<blocks, 256, 0, ex.stream>>>(o, v, ed, ed + o, shift, x);
   ex.count();
   CC_CUDA(cudaGetLastError());
-  CC_CUDA(cudaStreamSynchronize(ex.stream));  // e lives on the host stack
   // rotate back: b' = Uo c Uv^T
-  contract(ex, P64, 1.0, view(x, "ia", {o, v}), Uv("ca"), 0.0, view(w1, "ic", {o, v}));
-  contract(ex, P64, 1.0, Uo("ki"), view(w1, "ic", {o, v}), 0.0, view(x, "kc", {o, v}));
-  contract(ex, P64, 1.0, view(x + ov, "ijab", {o, o, v, v}), Uv("db"), 0.0, view(w2, "ijad", {o, o, v, v}));
-  contract(ex, P64, 1.0, Uv("ca"), view(w2, "ijad", {o, o, v, v}), 0.0, view(w1 + ov, "ijcd", {o, o, v, v}));
-  contract(ex, P64, 1.0, view(w1 + ov, "ijcd", {o, o, v, v}), Uo("lj"), 0.0, view(w2, "ilcd", {o, o, v, v}));
-  contract(ex, P64, 1.0, Uo("ki"), view(w2, "ilcd", {o, o, v, v}), 0.0, view(x + ov, "klcd", {o, o, v, v}));
+  contract(ex, rp, 1.0, view(x, "ia", {o, v}), Uv("ca"), 0.0, view(w1, "ic", {o, v}));
+  contract(ex, rp, 1.0, Uo("ki"), view(w1, "ic", {o, v}), 0.0, view(x, "kc", {o, v}));
+  contract(ex, rp, 1.0, view(x + ov, "ijab", {o, o, v, v}), Uv("db"), 0.0, view(w2, "ijad", {o, o, v, v}));
+  contract(ex, rp, 1.0, Uv("ca"), view(w2, "ijad", {o, o, v, v}), 0.0, view(w1 + ov, "ijcd", {o, o, v, v}));
+  contract(ex, rp, 1.0, view(w1 + ov, "ijcd", {o, o, v, v}), Uo("lj"), 0.0, view(w2, "ilcd", {o, o, v, v}));
+  contract(ex, rp, 1.0, Uo("ki"), view(w2, "ilcd", {o, o, v, v}), 0.0, view(x + ov, "klcd", {o, o, v, v}));
+  if (rp != CC_FP64) {
+    // A_F maps amplitudes with t_ij^ab = t_ji^ba to such amplitudes, and so does its exact
+    // inverse; rotations rounded on the tensor cores do not quite, so restore the symmetry
+    const size_t n2 = (size_t)o * o * v * v;
+    k_sym_add(ex, o, v, x + ov, w2, 0.0);
+    k_axpby(ex, n2, 0.5, w2, 0.0, x + ov);
+  }
 }
 
 void solve_AF(const Exec& ex, System& s, const double* b, double* x, cc_precision prec, double rtol, int m_max,
@@ -227,7 +235,7 @@ void solve_AF(const Exec& ex, System& s, const double* b, double* x, cc_precisio
   const size_t n = s.namp();
   if (direct) {
     DBuf<double> work(ex.pool, 2 * n);
-    solve_AF_direct(ex, s, b, x, 0.0, work.p);
+    solve_AF_direct(ex, s, b, x, 0.0, work.p, prec);
     if (st) st->af_applies += 1;
     return;
   }
@@ -258,10 +266,20 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
   double inner_rtol = opt.inner_rtol > 0 ? opt.inner_rtol
                                          : (opt.prec == CC_MIXED_TF32 ? 1e-6 : opt.prec == CC_MIXED_BF16X3 ? 1e-7 : opt.prec == CC_MIXED_TF32X3 ? 1e-8 : 1e-12);
   int inner_max = opt.inner_max > 0 ? opt.inner_max : 50;
+  const size_t n1 = (size_t)o * v;  // the singles block, dropped in CCD mode
+  // Every vector the Newton-Krylov iteration builds keeps t_ij^ab = t_ji^ba: R and J produce
+  // such vectors exactly (their doubles are symmetrised sums), and so would an exact A_F^{-1}.
+  // Inverses rounded on the tensor cores (mirror elements split or paired differently) are
+  // projected back, so the Krylov space never gains a spurious antisymmetric direction. FP64
+  // runs are left bit for bit as they are.
+  DBuf<double> symw(ex.pool, opt.prec == CC_FP64 ? 0 : n - n1);
   auto AFinv = [&](const double* b, double* x) {
     solve_AF(ex, s, b, x, opt.prec, inner_rtol, inner_max, opt.af_direct != 0, &st);
+    if (opt.prec != CC_FP64) {
+      k_sym_add(ex, o, v, x + n1, symw.p, 0.0);
+      k_axpby(ex, n - n1, 0.5, symw.p, 0.0, x + n1);
+    }
   };
-  const size_t n1 = (size_t)o * v;  // the singles block, dropped in CCD mode
   const cc_precision outer = opt.outer_prec == CC_DF64 ? CC_DF64 : CC_FP64;
   auto out_of_time = [&]() {
     return opt.max_seconds > 0 &&
