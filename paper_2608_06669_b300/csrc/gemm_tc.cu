@@ -176,16 +176,16 @@ __global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix
 // output row.
 template <typename T>
 __global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int splits, T* Cs,
-                                        long long kpad, int nseg, int seglo) {
+                                        long long kpad, int nseg, int seglo, int piece) {
   const int lane = threadIdx.x & 31;
   const size_t tot = (size_t)g.batch * g.M * g.N;
-  const int pieces = (g.N + ROW_PIECE - 1) / ROW_PIECE;
+  const int pieces = (g.N + piece - 1) / piece;
   const long long items = (long long)g.batch * g.M * pieces;
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long it = w0; it < items; it += nw) {
     const long long q = it / pieces;  // output row b * M + m
-    const int n0 = (int)(it - q * pieces) * ROW_PIECE, n1 = min(g.N, n0 + ROW_PIECE);
+    const int n0 = (int)(it - q * pieces) * piece, n1 = min(g.N, n0 + piece);
     const int b = (int)(q / g.M), m = (int)(q - (long long)b * g.M);
     const long long rowoff = cidx(g.cb, b) + cidx(g.cm, m);
     const float* pr = part + (size_t)q * g.N;
@@ -193,6 +193,7 @@ __global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ pa
     cw.init(g.cn, n0 + lane);
     for (int n = n0 + lane; n < n1; n += 32) {
       double s = 0.0;
+#pragma unroll 8
       for (int p = 0; p < splits; ++p) s += (double)pr[(size_t)p * tot + n];
       const long long off = rowoff + cw.off;
       if (Cs) {
@@ -608,17 +609,27 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   a.m_fast = a.num_m <= a.num_n ? 1 : 0;
   // split k when the output has fewer tiles than SMs and the sum is long: every split is a
   // tile of its own that writes FP32 partial sums, added in order by a second kernel. The
-  // factor minimises the waves of the persistent grid per unit of work, ceil(tiles s / SMs) / s
-  // (ties to the smaller factor), so the last wave is not left mostly idle.
+  // factor s minimises a time model of the persistent grid: waves(s) = ceil(tiles s / SMs)
+  // passes of (a tile's MMA time / s + a fixed per-tile cost for the pipeline fill and the
+  // epilogue), plus the HBM time of writing and re-reading the s partial sums.
   const long long base_tiles = (long long)a.num_m * a.num_n * g.batch;
   int splits = 1;
   if (base_tiles < ex.sm_count && a.kblocks >= 8) {
-    const int smax = (int)std::min<long long>(16, a.kblocks / 4);
-    double best = 1.0;
-    for (int sp = 2; sp <= smax; ++sp) {
+    const double sm_rate = (BF ? 2.0 : 1.0) * 5.8e12;  // dense MMA flop/s of one SM
+    const double t_tile = 2.0 * TM * TN * (double)a.kblocks * TK / sm_rate;
+    const double t_fix = 3e-6, hbm = 6.0e12;
+    const double part_bytes = 8.0 * (double)g.batch * g.M * g.N;  // FP32 written + read, per split
+    auto model = [&](int sp) {
       const double waves = (double)((base_tiles * sp + ex.sm_count - 1) / ex.sm_count);
-      if (waves / sp < best - 1e-9) {
-        best = waves / sp;
+      // the reduce: launch, partial-sum traffic, and one dependent load batch per 8 splits
+      return waves * (t_tile / sp + t_fix) + (sp > 1 ? (sp * part_bytes / hbm + 4e-6 + sp * 0.1e-6) : 0.0);
+    };
+    double best = model(1);
+    const int smax = (int)std::min<long long>(256, a.kblocks / 2);
+    for (int sp = 2; sp <= smax; ++sp) {
+      const double t = model(sp);
+      if (t < best * (1.0 - 1e-9)) {
+        best = t;
         splits = sp;
       }
     }
@@ -672,8 +683,13 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {
-    tc_splitk_reduce_kernel<T><<<blocks_for_rows((size_t)g.batch * g.M, g.N), 256, 0, ex.stream>>>(g, a.part, splits, static_cast<T*>(a.Cs),
-                                                                        a.cs_kpad, a.cs_nseg, a.cs_seglo);
+    // short outputs are cut into warp-sized pieces so that enough warps share the reads
+    const size_t rows = (size_t)g.batch * g.M;
+    const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
+    const size_t items = rows * ((g.N + piece - 1) / piece);
+    const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
+    tc_splitk_reduce_kernel<T><<<rblocks, 256, 0, ex.stream>>>(g, a.part, splits, static_cast<T*>(a.Cs), a.cs_kpad,
+                                                               a.cs_nseg, a.cs_seglo, piece);
     ex.count();
     CC_CUDA(cudaGetLastError());
   }
