@@ -58,60 +58,75 @@ __device__ __forceinline__ long long cidx(const CIdx& c, int x) {
   return (long long)i0 * c.s0 + (long long)i1 * c.s1 + (long long)i2 * c.s2;
 }
 
+// TMR x TNR outputs per thread on a 16 x 16 thread grid: a (16 TMR) x (16 TNR) tile. FP64 on
+// this part is so much slower than its loads and shared memory that even the smallest tile is
+// bound by the FMA pipe, so the host picks the tile that wastes the least on padding and
+// spreads the work most evenly over the SMs.
+template <int TMR, int TNR>
 __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  constexpr int TBM = 16 * TMR, TBN = 16 * TNR;
+  __shared__ double As[BK][TBM + 1];
+  __shared__ double Bs[BK][TBN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
   const int split = blockIdx.z % g.splits;
   const int kbeg = split * g.kchunk;
   const int kend = min(g.K, kbeg + g.kchunk);
 
   // per-thread load coordinates (fixed across k slices)
-  int a_mm[4], a_kk[4], b_nn[4], b_kk[4];
-  long long a_moff[4], b_noff[4];
+  // (TBM x BK = 256 TMR elements of A and 256 TNR of B per k slice)
+  int a_mm[TMR], a_kk[TMR], b_nn[TNR], b_kk[TNR];
+  long long a_moff[TMR], b_noff[TNR];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < TMR; ++r) {
     int e = tid + NT * r;
     if (g.a_kfast) { a_kk[r] = e % BK; a_mm[r] = e / BK; }
-    else           { a_mm[r] = e % BM; a_kk[r] = e / BM; }
-    if (g.b_kfast) { b_kk[r] = e % BK; b_nn[r] = e / BK; }
-    else           { b_nn[r] = e % BN; b_kk[r] = e / BN; }
-    int m = m0 + a_mm[r], n = n0 + b_nn[r];
+    else           { a_mm[r] = e % TBM; a_kk[r] = e / TBM; }
+    int m = m0 + a_mm[r];
     a_moff[r] = m < g.M ? cidx(g.am, m) : -1;
+  }
+#pragma unroll
+  for (int r = 0; r < TNR; ++r) {
+    int e = tid + NT * r;
+    if (g.b_kfast) { b_kk[r] = e % BK; b_nn[r] = e / BK; }
+    else           { b_nn[r] = e % TBN; b_kk[r] = e / TBN; }
+    int n = n0 + b_nn[r];
     b_noff[r] = n < g.N ? cidx(g.bn, n) : -1;
   }
 
   for (int bz = blockIdx.z / g.splits; bz < g.batch; bz += gridDim.z / g.splits) {
     const double* A = g.A + cidx(g.ab, bz);
     const double* B = g.B + cidx(g.bb, bz);
-    double acc[4][4];
+    double acc[TMR][TNR];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TMR; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < TNR; ++j) acc[i][j] = 0.0;
 
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < TMR; ++r) {
         int k = k0 + a_kk[r];
         As[a_kk[r]][a_mm[r]] = (a_moff[r] >= 0 && k < kend) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < TNR; ++r) {
         int kb = k0 + b_kk[r];
         Bs[b_kk[r]][b_nn[r]] = (b_noff[r] >= 0 && kb < kend) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0;
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double a[4], b[4];
+        double a[TMR], b[TNR];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+        for (int i = 0; i < TMR; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < TNR; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TMR; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < TNR; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -119,11 +134,11 @@ __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
       // partials [split][batch][M][N]
       double* P = g.part + ((size_t)split * g.batch + bz) * (size_t)g.M * g.N;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < TMR; ++i) {
         int m = m0 + ty + 16 * i;
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TNR; ++j) {
           int n = n0 + tx + 16 * j;
           if (n < g.N) P[(size_t)m * g.N + n] = acc[i][j];
         }
@@ -132,12 +147,12 @@ __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
     }
     double* C = g.C + cidx(g.cb, bz);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TMR; ++i) {
       int m = m0 + ty + 16 * i;
       if (m >= g.M) continue;
       long long cm = cidx(g.cm, m);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TNR; ++j) {
         int n = n0 + tx + 16 * j;
         if (n >= g.N) continue;
         double* c = C + cm + cidx(g.cn, n);
@@ -345,16 +360,44 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
     gemm_tc(ex, prec, g, tag);
     return;
   }
-  const long long tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
-  CC_REQUIRE(tm <= 65535, CC_ERR_INVALID, "gemm: M too large for the grid");
-  const long long tiles = tm * tn * g.batch;
-  const long long target = 4LL * ex.sm_count;  // two resident blocks per SM, two waves
   const int ksteps = (g.K + BK - 1) / BK;
-  int splits = 1;
-  if (tiles < target && ksteps >= 8) {
-    splits = (int)std::min<long long>((target + tiles - 1) / tiles, ksteps / 4);
-    splits = std::max(splits, 1);
+  // FP64: tile (16 TMR) x (16 TNR) and split-K factor from a model of the FMA-bound kernel:
+  // blocks are spread evenly over the SMs, so the time is ceil(blocks / SMs) blocks' FMA
+  // work (padding included) plus a small per-block cost, plus the split-K reduce (partial
+  // sums written and read, and a launch). Ties go to the larger tile and the fewer splits.
+  // The double-float kernel keeps its 64 x 64 tile and the occupancy-based split.
+  int tmr = 4, tnr = 4, splits = 1;
+  if (prec == CC_FP64) {
+    const double fma_rate = 2.0 * 2.0e9;  // FP64 FMAs per second of one SM
+    const double blk_cost = 2e-6, hbm = 6.0e12;
+    double best = 1e300;
+    const int smax = std::max(1, std::min(64, ksteps / 2));
+    for (int r : {4, 2, 1})
+      for (int c : {4, 2, 1}) {
+        const long long bm = 16 * r, bn = 16 * c;
+        const long long tiles = ((g.M + bm - 1) / bm) * ((g.N + bn - 1) / bn) * g.batch;
+        if ((g.M + bm - 1) / bm > 65535) continue;
+        for (int sp = 1; sp <= smax; ++sp) {
+          if (sp > 1 && tiles * sp > 16LL * ex.sm_count * 8) break;  // enough blocks already
+          const long long kst = (ksteps + sp - 1) / sp;
+          const double per_sm = (double)((tiles * sp + ex.sm_count - 1) / ex.sm_count);
+          double t = per_sm * ((double)bm * bn * BK * kst / fma_rate + blk_cost);
+          if (sp > 1) t += 16.0 * sp * (double)g.M * g.N * g.batch / hbm + 5e-6;
+          if (t < best * (1.0 - 1e-6)) {
+            best = t;
+            tmr = r;
+            tnr = c;
+            splits = sp;
+          }
+        }
+      }
+  } else {
+    const long long tiles = (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * g.batch;
+    const long long target = 4LL * ex.sm_count;  // two resident blocks per SM, two waves
+    if (tiles < target && ksteps >= 8) splits = (int)std::max<long long>(1, std::min<long long>((target + tiles - 1) / tiles, ksteps / 4));
   }
+  const long long tm = (g.M + 16 * tmr - 1) / (16 * tmr), tn = (g.N + 16 * tnr - 1) / (16 * tnr);
+  CC_REQUIRE(tm <= 65535, CC_ERR_INVALID, "gemm: M too large for the grid");
   DBuf<double> part;
   g.splits = splits;
   g.kchunk = ((ksteps + splits - 1) / splits) * BK;
@@ -366,8 +409,15 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
   dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)(zb * splits));
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
-  if (prec == CC_DF64) gemm_df64_kernel<<<grid, NT, 0, ex.stream>>>(g);
-  else gemm_f64_kernel<<<grid, NT, 0, ex.stream>>>(g);
+  if (prec == CC_DF64) {
+    gemm_df64_kernel<<<grid, NT, 0, ex.stream>>>(g);
+  } else {
+    auto k = gemm_f64_kernel<4, 4>;
+    if (tmr == 4) k = tnr == 4 ? gemm_f64_kernel<4, 4> : tnr == 2 ? gemm_f64_kernel<4, 2> : gemm_f64_kernel<4, 1>;
+    else if (tmr == 2) k = tnr == 4 ? gemm_f64_kernel<2, 4> : tnr == 2 ? gemm_f64_kernel<2, 2> : gemm_f64_kernel<2, 1>;
+    else k = tnr == 4 ? gemm_f64_kernel<1, 4> : tnr == 2 ? gemm_f64_kernel<1, 2> : gemm_f64_kernel<1, 1>;
+    k<<<grid, NT, 0, ex.stream>>>(g);
+  }
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {
