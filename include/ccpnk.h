@@ -118,14 +118,21 @@ const char* cc_last_error(const cc_ctx* ctx);
 size_t cc_ctx_device_bytes(const cc_ctx* ctx);
 /* Number of kernel launches the context has issued since it was created. */
 uint64_t cc_ctx_launches(const cc_ctx* ctx);
-/* Kernel timer (tracing): enable != 0 clears the records and brackets every tagged launch
- * with CUDA events on the context's stream; enable = 0 turns it off. Tags in use:
- * "ladder_build.<p>" and "ladder_contract.<p>" (the two GEMMs of the particle-particle
- * ladder, <p> = fp64 or tf32). */
+/* Kernel timer (tracing): enable != 0 clears the records and brackets every GEMM launch
+ * with CUDA events on the context's stream; enable = 0 turns it off. Tags: "ladder_build.<p>"
+ * and "ladder_contract.<p>" (the two GEMMs of the particle-particle ladder, <p> = fp64, df64,
+ * tf32 or bf16), and for every other contraction its index labels and kernel family, e.g.
+ * "kc*Pkd>Pcd.f64" (A labels * B labels > C labels; .f64, .df64 or .tc). The time of a
+ * tensor-core launch covers the GEMM and its split-k reduce, not the operand staging. */
 int cc_ctx_profile(cc_ctx* ctx, int enable);
 /* Launch count, summed event time (ms) and summed algorithmic flops of one tag since the
  * last cc_ctx_profile(ctx, 1). Waits for the recorded launches to finish. */
 int cc_ctx_profile_get(cc_ctx* ctx, const char* tag, uint64_t* launches, double* total_ms, double* flops);
+/* Every tag recorded since the last cc_ctx_profile(ctx, 1), one line each as
+ * "tag<TAB>launches<TAB>total_ms<TAB>flops<LF>", written to buf (cap bytes, NUL-terminated,
+ * truncated at a line boundary). *needed (may be NULL) receives the full length + 1. A
+ * diagnostic of this library: the paper has no counterpart. */
+int cc_ctx_profile_list(cc_ctx* ctx, char* buf, size_t cap, size_t* needed);
 
 /* A problem resident on the device: copies fock (n x n) and B (naux x n x n), host or device.
  * Its device memory comes from the context's pool, so every cc_sys of a context must be

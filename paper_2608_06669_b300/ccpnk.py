@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
             "cc_ctx_launches": (u64, [vp]),
             "cc_ctx_profile": (i, [vp, i]),
             "cc_ctx_profile_get": (i, [vp, ctypes.c_char_p, ctypes.POINTER(u64), ctypes.POINTER(d), ctypes.POINTER(d)]),
+            "cc_ctx_profile_list": (i, [vp, ctypes.c_char_p, sz, ctypes.POINTER(sz)]),
             "cc_sys_create": (i, [vp, i, i, i, vp, vp, pp]),
             "cc_sys_destroy": (None, [vp]),
             "cc_residual": (i, [vp, vp, vp, vp, vp, vp, ctypes.POINTER(d), i]),
@@ -176,6 +177,18 @@ class Context:
         _check(self.h, lib().cc_ctx_profile_get(self.h, tag.encode(), ctypes.byref(n), ctypes.byref(ms),
                                                 ctypes.byref(fl)))
         return int(n.value), float(ms.value), float(fl.value)
+
+    def profile_list(self):
+        """{tag: (launches, total_ms, flops)} for every tag recorded since profile(True)."""
+        need = ctypes.c_size_t()
+        _check(self.h, lib().cc_ctx_profile_list(self.h, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(self.h, lib().cc_ctx_profile_list(self.h, buf, need.value, None))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            tag, n, ms, fl = line.split("\t")
+            out[tag] = (int(n), float(ms), float(fl))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -295,6 +295,28 @@ int cc_ctx_profile_get(cc_ctx* ctx, const char* tag, uint64_t* launches, double*
   });
 }
 
+int cc_ctx_profile_list(cc_ctx* ctx, char* buf, size_t cap, size_t* needed) {
+  if (!ctx || (!buf && cap)) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    ctx->prof.resolve();
+    std::string all;
+    size_t fit = 0;  // length of the whole lines that fit in buf
+    for (auto& d : ctx->prof.done) {
+      char line[512];
+      snprintf(line, sizeof line, "%s\t%llu\t%.6f\t%.6e\n", d.first.c_str(), (unsigned long long)d.second.launches,
+               d.second.ms, d.second.flops);
+      all += line;
+      if (all.size() < cap) fit = all.size();
+    }
+    if (cap) {
+      memcpy(buf, all.data(), fit);
+      buf[fit] = '\0';
+    }
+    if (needed) *needed = all.size() + 1;
+    return CC_OK;
+  });
+}
+
 int cc_sys_create(cc_ctx* ctx, int o, int v, int naux, const double* fock, const double* B, cc_sys** out) {
   if (!ctx || !out) return CC_ERR_INVALID;
   *out = nullptr;

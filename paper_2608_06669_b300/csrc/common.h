@@ -224,6 +224,8 @@ int k_energy_partials(const Exec& ex, int o, int v);
 // scaled elementwise divide: y = x / (D + shift) with D built from diagonal Fock entries
 void k_denom_divide(const Exec& ex, int o, int v, const double* fdiag, double shift,
                     const double* x1, const double* x2, double* y1, double* y2, double scale);
+// out[i][j][a][b] = scale * g[i][a][j][b]
+void k_ovov_to_oovv(const Exec& ex, int o, int v, const double* g, double* out, double scale);
 // copy a (rows x cols) block with strides
 void k_copy2d(const Exec& ex, int rows, int cols, const double* src, long long lds, double* dst,
               long long ldd);

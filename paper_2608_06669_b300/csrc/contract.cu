@@ -357,8 +357,25 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   CC_REQUIRE(!((g.so || g.sb) && (prec == CC_FP64 || prec == CC_DF64)), CC_ERR_INVALID, "staged operands need a tensor-core precision");
   if (prec != CC_FP64 && prec != CC_DF64) {
-    gemm_tc(ex, prec, g, tag);
-    return;
+    // A contraction too thin for 128 x 256 tensor-core tiles (a short k, or a narrow M or
+    // N) costs more in staging, padding and launch latency than it saves: if the FP64
+    // kernel is estimated to be faster it runs there (more accurate, never less).
+    const double flops = 2.0 * g.M * (double)g.N * g.K * g.batch;
+    const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
+    const int tk = prec == CC_MIXED_BF16X3 ? 64 : 32;
+    const double padded = 2.0 * ((g.M + 127) / 128 * 128.0) * ((g.N + 255) / 256 * 256.0) *
+                          ((g.K + tk - 1) / tk * (double)tk) * nseg * g.batch;
+    const double t_tc = 12e-6 + padded / 4.5e14 + 8.0 * g.M * (double)g.N * g.batch / 1e12;
+    // the FP64 kernel's parallelism: 16 x 16 tiles, k split at most 64 ways
+    const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch *
+                          std::min(64, std::max(1, g.K / 32));
+    const double flops16 = 2.0 * ((g.M + 15) / 16 * 16.0) * ((g.N + 15) / 16 * 16.0) * g.K * g.batch;
+    const double t_f64 = 4e-6 + flops16 / (1.0e12 * std::min(1.0, blocks / ex.sm_count));
+    if (g.so || g.sb || t_tc <= t_f64) {
+      gemm_tc(ex, prec, g, tag);
+      return;
+    }
+    prec = CC_FP64;
   }
   const int ksteps = (g.K + BK - 1) / BK;
   // FP64: tile (16 TMR) x (16 TNR) and split-K factor from a model of the FMA-bound kernel:
@@ -435,6 +452,12 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
 
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
               double beta, const TView& C, const char* tag, const StagedOut* so, const StagedIn* sb) {
+  std::string auto_tag;  // with the timer on, an untagged contraction is named by its labels
+  if (!tag && ex.prof && ex.prof->on) {
+    auto_tag = std::string(A.lab) + "*" + B.lab + ">" + C.lab +
+               (prec == CC_FP64 ? ".f64" : prec == CC_DF64 ? ".df64" : ".tc");
+    tag = auto_tag.c_str();
+  }
   auto find = [](const TView& t, char l) {
     for (int d = 0; d < t.nd; ++d)
       if (t.lab[d] == l) return d;

@@ -403,6 +403,23 @@ void k_denom_divide(const Exec& ex, int o, int v, const double* fdiag, double sh
   denom_divide_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, fdiag, shift, x1, x2, y1, y2, scale);
   LAUNCH_CHECK();
 }
+__global__ void ovov_to_oovv_kernel(int o, int v, const double* __restrict__ g, double* __restrict__ out, double scale) {
+  const size_t n = (size_t)o * o * v * v;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e % v);
+    size_t q = e / v;
+    const int a = (int)(q % v);
+    q /= v;
+    const int j = (int)(q % o), i = (int)(q / o);
+    out[e] = scale * g[(((size_t)i * v + a) * o + j) * v + b];
+  }
+}
+void k_ovov_to_oovv(const Exec& ex, int o, int v, const double* g, double* out, double scale) {
+  const size_t n = (size_t)o * o * v * v;
+  if (!n) return;
+  ovov_to_oovv_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, g, out, scale);
+  LAUNCH_CHECK();
+}
 void k_copy2d(const Exec& ex, int rows, int cols, const double* src, long long lds, double* dst, long long ldd) {
   size_t n = (size_t)rows * cols;
   if (!n) return;

@@ -296,12 +296,13 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     return std::sqrt(std::max(hv[0], 0.0));
   };
 
-  // generalised MP2 start (Eq. inexact_newton_update at t = 0): t1 = 0, t2 = A_F^{-1}(-R2(0))
+  // generalised MP2 start (Eq. inexact_newton_update at t = 0): t1 = 0, t2 = A_F^{-1}(-R2(0)).
+  // At t = 0 every amplitude term of the residual vanishes and R2(0)_ij^ab = (ia|jb), so the
+  // start needs no residual evaluation.
   if (!use_guess) {
     k_fill(ex, n, 0.0, t);
-    residual(t, r.p, nullptr);
-    k_fill(ex, (size_t)o * v, 0.0, r.p);
-    k_scale(ex, n, -1.0, r.p);
+    k_fill(ex, n1, 0.0, r.p);
+    k_ovov_to_oovv(ex, o, v, s.Govov.p, r.p + n1, -1.0);
     AFinv(r.p, t);
   } else if (opt.ccd) {
     k_fill(ex, n1, 0.0, t);
