@@ -143,6 +143,24 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
     }
   }
   void* W2 = W2_.p;
+  // FP64 and double-float: (c, d) split into the parts symmetric (+) and antisymmetric (-)
+  // under c <-> d. Since T_ij^cd = T_ji^dc, T+ is symmetric and T- antisymmetric in (i, j), so
+  // L = sum_{c<=d} W+ T+ + sum_{c<d} W- T- is contracted over pairs i <= j and c <= d only:
+  // half the flops of the (c, d) contraction.
+  const int Po = o * (o + 1) / 2, Qo = o * (o - 1) / 2, Pv = v * (v + 1) / 2, Qv = v * (v - 1) / 2;
+  double* Tp = nullptr;
+  double* Tmn = nullptr;
+  if (!tensor) {
+    const size_t nbmax = (size_t)ladder_block_ * v;
+    if (!pmW_.p) {
+      pmT_.alloc(ex_.pool, (size_t)Po * Pv + (size_t)Qo * Qv + 1);
+      pmW_.alloc(ex_.pool, nbmax * (size_t)(Pv + Qv) + 1);
+      pmL_.alloc(ex_.pool, (size_t)(Po + Qo) * nbmax + 1);
+    }
+    Tp = pmT_.p;
+    Tmn = Tp + (size_t)Po * Pv;
+    k_ladder_pm_T(ex_, o, v, T, Tp, Tmn);
+  }
   for (int a0 = 0; a0 < v; a0 += ladder_block_) {
     const int al = std::min(ladder_block_, v - a0);
     const int bl = v - a0;  // b in [a0, v)
@@ -153,7 +171,19 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
     TView W = view(W_.p, "abcd", {al, bl, v, v});
     if (!tensor) {
       contract(ex_, prec, 1.0, Xa, Yb, 0.0, W, tb);
-      contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc);
+      const int nb = al * bl;
+      double* Wp = pmW_.p;
+      double* Wm = Wp + (size_t)nb * Pv;
+      k_ladder_pm_W(ex_, nb, v, W_.p, Wp, Wm);
+      double* Lp = pmL_.p;
+      double* Lm = Lp + (size_t)Po * nb;
+      contract(ex_, prec, 1.0, view(Tp, "xq", {Po, Pv}), view(Wp, "nq", {nb, Pv}), 0.0, view(Lp, "xn", {Po, nb}), tc);
+      if (Qo > 0 && Qv > 0)
+        contract(ex_, prec, 1.0, view(Tmn, "xq", {Qo, Qv}), view(Wm, "nq", {nb, Qv}), 0.0, view(Lm, "xn", {Qo, nb}),
+                 tc);
+      else if (Qo > 0)
+        k_fill(ex_, (size_t)Qo * nb, 0.0, Lm);
+      k_ladder_pm_unpack(ex_, o, v, a0, al, bl, Lp, Lm, L);
       continue;
     }
     // W2[(a,b)][s * kpad + c v + d]: the strides below count floats of W2

@@ -53,6 +53,7 @@ class Engine {
   int ladder_block_ = 1;
   Pair t_, u_, Btoo_, Btvv_, Btvo_, gam_, hY_, Ft_, Z_, Wk_, Woo_, Cint_, Dint_, Gv_, Go_, X_, Y2_;
   DBuf<double> W_;        // ladder workspace, ladder_block_ * v^3
+  DBuf<double> pmT_, pmW_, pmL_;  // the FP64 ladder's (c, d)-split operands and results
   DBuf<double> XsYs_;     // stacked factors of the tangent ladder
   DBuf<double> W2_;       // tensor-core ladder slab in staging layout (TF32 or BF16 words)
   int w2_mode_ = -1;      // precision whose layout W2_ holds

@@ -204,6 +204,12 @@ void k_sym_add(const Exec& ex, int o, int v, const double* X, double* out, doubl
 void k_make_u(const Exec& ex, int o, int v, const double* t, double* u);
 // R[i][j][a][b] += L[i][j][a][b] if b >= (a / blk) * blk, else L[j][i][b][a] (the ladder's mirror)
 void k_ladder_mirror_add(const Exec& ex, int o, int v, int blk, const double* L, double* R);
+// The ladder's symmetric/antisymmetric split over (c, d): pair-packed T+, T- (rows i <= j and
+// i < j), W+, W- (per slab row), and the block of L rebuilt from L+ and L-
+void k_ladder_pm_T(const Exec& ex, int o, int v, const double* T, double* Tp, double* Tm);
+void k_ladder_pm_W(const Exec& ex, size_t rows, int v, const double* W, double* Wp, double* Wm);
+void k_ladder_pm_unpack(const Exec& ex, int o, int v, int a0, int al, int bl, const double* Lp, const double* Lm,
+                        double* L);
 // L[p][q][r][s] = 2 g[p][q][r][s] - g[p][s][r][q] over an (o v o v) block
 void k_make_L_ovov(const Exec& ex, int o, int v, const double* g, double* L);
 // gamma[P] = sum_k A[P][k][k]

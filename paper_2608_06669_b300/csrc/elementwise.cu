@@ -74,6 +74,62 @@ __global__ void ladder_mirror_add_kernel(int o, int v, int blk, const double* __
   }
 }
 
+// Pair indices, row-major over the upper triangle: c <= d (with the diagonal) and c < d.
+__device__ __forceinline__ size_t pair_le(int c, int d, int n) { return (size_t)c * (2 * n - c + 1) / 2 + (d - c); }
+__device__ __forceinline__ size_t pair_lt(int c, int d, int n) { return (size_t)c * (2 * n - c - 1) / 2 + (d - c - 1); }
+
+// T+[(i<=j)][(c<=d)] = (T_ij^cd + T_ij^dc) / 2 (T_ij^cc on the diagonal), T-[(i<j)][(c<d)] =
+// (T_ij^cd - T_ij^dc) / 2, for T with T_ij^cd = T_ji^dc
+__global__ void ladder_pm_T_kernel(int o, int v, const double* __restrict__ T, double* __restrict__ Tp,
+                                   double* __restrict__ Tm) {
+  const size_t n = (size_t)o * o * v * v;
+  const size_t Pv = (size_t)v * (v + 1) / 2, Qv = (size_t)v * (v - 1) / 2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int d = (int)(e % v);
+    size_t r = e / v;
+    const int c = (int)(r % v);
+    r /= v;
+    const int j = (int)(r % o), i = (int)(r / o);
+    if (i > j || c > d) continue;
+    const double x = T[e], y = T[(((size_t)i * o + j) * v + d) * v + c];
+    Tp[pair_le(i, j, o) * Pv + pair_le(c, d, v)] = c < d ? 0.5 * (x + y) : x;
+    if (i < j && c < d) Tm[pair_lt(i, j, o) * Qv + pair_lt(c, d, v)] = 0.5 * (x - y);
+  }
+}
+
+// W+[r][(c<=d)] = W_r^cd + W_r^dc (W_r^cc on the diagonal), W-[r][(c<d)] = W_r^cd - W_r^dc
+__global__ void ladder_pm_W_kernel(size_t rows, int v, const double* __restrict__ W, double* __restrict__ Wp,
+                                   double* __restrict__ Wm) {
+  const size_t vv = (size_t)v * v, n = rows * vv;
+  const size_t Pv = (size_t)v * (v + 1) / 2, Qv = (size_t)v * (v - 1) / 2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int d = (int)(e % v);
+    const size_t q = e / v;
+    const int c = (int)(q % v);
+    const size_t r = q / v;
+    if (c > d) continue;
+    const double x = W[e], y = W[r * vv + (size_t)d * v + c];
+    Wp[r * Pv + pair_le(c, d, v)] = c < d ? x + y : x;
+    if (c < d) Wm[r * Qv + pair_lt(c, d, v)] = x - y;
+  }
+}
+
+// L[i][j][a0 + a][a0 + b] = L+[(i<=j)][n] + L-[(i<j)][n] for i <= j and L+[(j<=i)][n] -
+// L-[(j<i)][n] for i > j, n = a bl + b (L+ symmetric and L- antisymmetric in i, j)
+__global__ void ladder_pm_unpack_kernel(int o, int v, int a0, int al, int bl, const double* __restrict__ Lp,
+                                        const double* __restrict__ Lm, double* __restrict__ L) {
+  const size_t nb = (size_t)al * bl, n = (size_t)o * o * nb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t nn = e % nb, ij = e / nb;
+    const int j = (int)(ij % o), i = (int)(ij / o);
+    const int a = (int)(nn / bl), b = (int)(nn % bl);
+    double val;
+    if (i <= j) val = Lp[pair_le(i, j, o) * nb + nn] + (i < j ? Lm[pair_lt(i, j, o) * nb + nn] : 0.0);
+    else val = Lp[pair_le(j, i, o) * nb + nn] - Lm[pair_lt(j, i, o) * nb + nn];
+    L[(((size_t)i * o + j) * v + a0 + a) * v + a0 + b] = val;
+  }
+}
+
 // u[i][j][a][b] = 2 t[i][j][a][b] - t[j][i][a][b]
 __global__ void make_u_kernel(int o, int v, const double* __restrict__ t, double* __restrict__ u) {
   size_t n = (size_t)o * o * v * v;
@@ -347,6 +403,25 @@ void k_ladder_mirror_add(const Exec& ex, int o, int v, int blk, const double* L,
   size_t n = (size_t)o * o * v * v;
   if (!n) return;
   ladder_mirror_add_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, blk, L, R);
+  LAUNCH_CHECK();
+}
+void k_ladder_pm_T(const Exec& ex, int o, int v, const double* T, double* Tp, double* Tm) {
+  const size_t n = (size_t)o * o * v * v;
+  if (!n) return;
+  ladder_pm_T_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, T, Tp, Tm);
+  LAUNCH_CHECK();
+}
+void k_ladder_pm_W(const Exec& ex, size_t rows, int v, const double* W, double* Wp, double* Wm) {
+  const size_t n = rows * v * v;
+  if (!n) return;
+  ladder_pm_W_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(rows, v, W, Wp, Wm);
+  LAUNCH_CHECK();
+}
+void k_ladder_pm_unpack(const Exec& ex, int o, int v, int a0, int al, int bl, const double* Lp, const double* Lm,
+                        double* L) {
+  const size_t n = (size_t)o * o * al * bl;
+  if (!n) return;
+  ladder_pm_unpack_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, a0, al, bl, Lp, Lm, L);
   LAUNCH_CHECK();
 }
 void k_make_u(const Exec& ex, int o, int v, const double* t, double* u) {

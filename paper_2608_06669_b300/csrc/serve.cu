@@ -45,7 +45,7 @@ size_t footprint_bytes(int o, int v, int naux, const cc_solve_opts& op) {
   double doubles = 0;
   doubles += 3.0 * naux * n * n;                            // B (upload, blocks)
   doubles += 36.0 * oovv + 8.0 * naux * n * n;              // engine values + tangents
-  doubles += lb * v * v * v;                                // ladder slab
+  doubles += 2.0 * lb * v * v * v;                          // ladder slab and its (c, d) split
   if (op.prec != CC_FP64 && op.prec != CC_DF64)             // its tensor-core staging copy
     doubles += std::ceil(lb * v / 256.0) * 256.0 * 3.0 * std::ceil((double)v * v / 64.0) * 64.0 / 2.0;
   doubles += (op.m_max + 8.0) * namp;                       // outer Krylov basis and vectors
