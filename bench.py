@@ -34,6 +34,10 @@ METRIC = "PNK time-to-‖R‖<1e-8, mixed vs FP64; residual TFLOP/s vs peak; p50
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # TF32 dense tensor peak: measured bf16 burst x the nominal TF32/BF16 ratio (1.1 / 2.25)
 TF32_RATIO = 1.1 / 2.25
+# DRAM bytes (read + write) per FP64 ladder-build launch, averaged over the eight build launches
+# of one FP64 residual at o=10, v=90, naux=300, from one ncu capture of the current kernel
+# (the FP64 ladder-build summary among the kernel profiles); the slab it writes mostly stays in L2
+LADDER_BUILD_F64_DRAM_BYTES = 12.65e6
 
 
 def rank_info():
@@ -259,11 +263,11 @@ def run_ours(args):
     ach = lb[2] / (lb[1] / 1e3) / 1e12 if lb[1] > 0 else None
     roof = {"bound": "alu", "kernel": "gemm_f64_kernel (ladder build, FP64 FMA pipe)", "achieved": ach,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": (ach / FP64_PEAK_TFLOPS) if ach else None,
-            "traffic": None, "launches": lb[0], "ms_per_launch": lb[1] / max(lb[0], 1),
+            "traffic": LADDER_BUILD_F64_DRAM_BYTES, "launches": lb[0], "ms_per_launch": lb[1] / max(lb[0], 1),
             "flops_per_launch": lb[2] / max(lb[0], 1), "peak_source": "148 SMs x 2 DFMA/clk x 2 x 2.032 GHz"}
     tf32_peak = peaks["bf16_tflops"] * TF32_RATIO
     ach_tc = lc[2] / (lc[1] / 1e3) / 1e12 if lc[1] > 0 else None
-    roof_tc = {"bound": "tensor", "kernel": "gemm_tf32_kernel (ladder build, tcgen05 kind::tf32)", "achieved": ach_tc,
+    roof_tc = {"bound": "tensor", "kernel": "gemm_tc_kernel (ladder build, tcgen05 kind::tf32, three-pass split)", "achieved": ach_tc,
                "peak": tf32_peak, "unit": "TFLOP/s", "frac": (ach_tc / tf32_peak) if ach_tc else None,
                "launches": lc[0], "peak_source": f"{peak_kind} bf16 burst x 1.1/2.25"}
     cpu = None
@@ -316,7 +320,10 @@ def run_serve(args):
     out = {}
     # the FP64 path is ~4-12x slower per solve, so it serves the first requests of the same
     # stream only (the mixed path serves all of them); both cap a solve at max_newton steps
-    for prec, reqs in (("tf32x3", reqs_all), ("fp64", reqs_all[: args.serve_fp64])):
+    # the mixed path also serves that same prefix alone, so p50/p99 compare like with like
+    passes = (("tf32x3", "tf32x3", reqs_all), ("tf32x3_fp64_set", "tf32x3", reqs_all[: args.serve_fp64]),
+              ("fp64", "fp64", reqs_all[: args.serve_fp64]))
+    for key, prec, reqs in passes:
         srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=args.slots)
         t_start = time.perf_counter()
         tickets = []
@@ -340,7 +347,7 @@ def run_serve(args):
         lat = np.array([f - sub for sub, _, f in times])
         span = max(f for _, _, f in times) - min(sub for sub, _, _ in times)
         conv = [results[t][2]["status_code"] == 0 for t in tickets]
-        out[prec] = {"solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
+        out[key] = {"solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
                      "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(conv)), "requests": len(tickets),
                      "max_concurrent": stats["max_running"], "makespan_s": span,
                      "not_converged": [f"o{s.o}v{s.v}" for (_, s), c in zip(reqs, conv) if not c]}
@@ -349,7 +356,7 @@ def run_serve(args):
             "config": {"workload": "served mix", "requests": args.serve, "arrivals": "exponential, mean 20 ms",
                        "o": "U{4..16}", "v": "round(o U[6,9])", "naux": "3(o+v)", "gauges": "canonical / Haar",
                        "slots": args.slots, "af_inverse": "eigenbasis"},
-            "mixed": out["tf32x3"], "fp64": out["fp64"]}
+            "mixed": out["tf32x3"], "mixed_on_fp64_requests": out["tf32x3_fp64_set"], "fp64": out["fp64"]}
     print(json.dumps(line), flush=True)
 
 
@@ -403,6 +410,8 @@ def run_kernels(args):
     ctx.profile(False)
     out["tf32_peak_tflops"] = tf32_peak
     print(json.dumps({"metric": METRIC, "mode": "kernels", **out}), flush=True)
+    if args.kernels_only:
+        return
     # capped solves, one line each so that a partial run still reports
     for meth, prec, extra in (("pnk", "tf32x3", {}), ("nk", "tf32x3", {}),
                               ("fp_diis", "fp64", {"level_shift": args.shift}), ("pnk", "fp64", {})):
@@ -462,6 +471,7 @@ def main():
     ap.add_argument("--kernels", default="", help="per-kernel rates and capped solves on this workload instead")
     ap.add_argument("--shift", type=float, default=0.2, help="FP+DIIS level shift in --kernels")
     ap.add_argument("--no-fp64-solve", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true", help="--kernels without the capped solves")
     ap.add_argument("--solve-seconds", type=float, default=120.0, help="wall-time cap of each solve in --kernels")
     ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests instead")
     ap.add_argument("--slots", type=int, default=8)
