@@ -161,8 +161,9 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
     Tmn = Tp + (size_t)Po * Pv;
     k_ladder_pm_T(ex_, o, v, T, Tp, Tmn);
   }
-  for (int a0 = 0; a0 < v; a0 += ladder_block_) {
-    const int al = std::min(ladder_block_, v - a0);
+  const int blk = ladder_block_;
+  for (int a0 = 0; a0 < v; a0 += blk) {
+    const int al = std::min(blk, v - a0);
     const int bl = v - a0;  // b in [a0, v)
     TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {Paux, al, v}, {(long long)v * v, v, 1});
     TView Yb = view_strided(Y + (size_t)a0 * v, "Pbd", {Paux, bl, v}, {(long long)v * v, v, 1});
@@ -193,7 +194,7 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
     StagedIn sb{W2, rows_pad, (int)kk};
     contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc, nullptr, &sb);
   }
-  k_ladder_mirror_add(ex_, o, v, ladder_block_, L, R);
+  k_ladder_mirror_add(ex_, o, v, blk, L, R);
 }
 
 void Engine::program(bool tan, cc_precision prec, double* rout) {

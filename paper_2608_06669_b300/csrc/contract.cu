@@ -276,6 +276,54 @@ __global__ void __launch_bounds__(NT, 2) gemm_df64_kernel(GemmArgs g) {
   }
 }
 
+// Matrix-vector contractions (N == 1, or M == 1 with the operands' roles swapped): bound by
+// reading the matrix once, so the GEMM tiles (15/16 of them idle on the unit dimension) are
+// the wrong shape. Each output element is one warp (lanes walk k, then a fixed shuffle tree)
+// when the matrix is contiguous along k, else one thread (k walked in order), so consecutive
+// threads read consecutive rows. Either way the sum order is fixed: results are reproducible.
+__global__ void gemv_f64_kernel(GemmArgs g, int trans, int warp_per_row) {
+  const int rows = trans ? g.N : g.M;
+  const long long nout = (long long)rows * g.batch;
+  // the matrix operand (indexed by row and k) and the vector operand (by k)
+  const double* Mx = trans ? g.B : g.A;
+  const double* Vx = trans ? g.A : g.B;
+  const CIdx& mr = trans ? g.bn : g.am;  // row index of the matrix
+  const CIdx& mk = trans ? g.bk : g.ak;
+  const CIdx& mb = trans ? g.bb : g.ab;
+  const CIdx& vk = trans ? g.ak : g.bk;
+  const CIdx& vb = trans ? g.ab : g.bb;
+  const long long v0 = trans ? cidx(g.am, 0) : cidx(g.bn, 0);  // the vector's fixed row/column
+  const long long c0 = trans ? cidx(g.cm, 0) : cidx(g.cn, 0);
+  const CIdx& cr = trans ? g.cn : g.cm;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const long long step = warp_per_row ? nth / 32 : nth;
+  for (long long e = warp_per_row ? tid / 32 : tid; e < nout; e += step) {
+    const int b = (int)(e / rows), r = (int)(e - (long long)b * rows);
+    const double* mrow = Mx + cidx(mb, b) + cidx(mr, r);
+    const double* vrow = Vx + cidx(vb, b) + v0;
+    double s = 0.0;
+    CWalk wm, wv;
+    const int k0 = warp_per_row ? lane : 0, dk = warp_per_row ? 32 : 1;
+    wm.init(mk, k0);
+    wv.init(vk, k0);
+    for (int k = k0; k < g.K; k += dk) {
+      s = fma(mrow[wm.off], vrow[wv.off], s);
+      wm.step(mk, dk);
+      wv.step(vk, dk);
+    }
+    if (warp_per_row) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane != 0) continue;
+    }
+    double* c = g.C + cidx(g.cb, b) + c0 + cidx(cr, r);
+    const double val = g.alpha * s;
+    *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
+  }
+}
+
 // C = alpha * sum_s part[s] + beta * C, the splits added in order
 __global__ void splitk_reduce_kernel(GemmArgs g) {
   const size_t per = (size_t)g.M * g.N;
@@ -370,12 +418,31 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
     const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch *
                           std::min(64, std::max(1, g.K / 32));
     const double flops16 = 2.0 * ((g.M + 15) / 16 * 16.0) * ((g.N + 15) / 16 * 16.0) * g.K * g.batch;
-    const double t_f64 = 4e-6 + flops16 / (1.0e12 * std::min(1.0, blocks / ex.sm_count));
+    double t_f64 = 4e-6 + flops16 / (1.0e12 * std::min(1.0, blocks / ex.sm_count));
+    if ((g.N == 1 || g.M == 1) && (long long)(g.N == 1 ? g.M : g.N) * g.batch >= 256)
+      t_f64 = 4e-6 + 8.0 * (g.N == 1 ? g.M : g.N) * (double)g.K * g.batch / 2e12;  // the FP64 GEMV reads the matrix once
     if (g.so || g.sb || t_tc <= t_f64) {
       gemm_tc(ex, prec, g, tag);
       return;
     }
     prec = CC_FP64;
+  }
+  // (a few outputs over a long k stay on the split-k GEMM path, which spreads k over SMs)
+  if (prec == CC_FP64 && (g.N == 1 || g.M == 1) && g.K > 0 &&
+      (long long)(g.N == 1 ? g.M : g.N) * g.batch >= 256) {
+    const int trans = g.N == 1 ? 0 : 1;
+    const long long nout = (long long)(trans ? g.N : g.M) * g.batch;
+    const CIdx& mk = trans ? g.bk : g.ak;
+    const int wpr = inner_stride(mk) == 1 ? 1 : 0;
+    const long long threads = wpr ? nout * 32 : nout;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((threads + 255) / 256, (long long)ex.sm_count * 16));
+    cudaEvent_t ev = nullptr;
+    if (ex.timing(tag)) ex.mark_begin(&ev);
+    gemv_f64_kernel<<<blocks, 256, 0, ex.stream>>>(g, trans, wpr);
+    ex.count();
+    CC_CUDA(cudaGetLastError());
+    if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
+    return;
   }
   const int ksteps = (g.K + BK - 1) / BK;
   // FP64: tile (16 TMR) x (16 TNR) and split-K factor from a model of the FMA-bound kernel:

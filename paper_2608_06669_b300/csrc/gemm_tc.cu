@@ -90,43 +90,6 @@ __device__ __forceinline__ void store_staged(T* p, long long kpad, int nseg, int
   for (int s = 0; s < nseg; ++s) p[(long long)s * kpad] = ((seglo >> s) & 1) ? lo : hi;
 }
 
-// Offsets of a compound index walked in steps of a fixed size: the mixed-radix digits are
-// carried forward instead of divided out for every element (a division only on a carry).
-struct CWalk {
-  long long off;
-  int i0, i1, i2;
-  __device__ __forceinline__ void init(const CIdx& c, int x) {
-    if (c.e1 == 1 && c.e2 == 1) {
-      i0 = x;
-      i1 = i2 = 0;
-    } else {
-      i2 = x % c.e2;
-      const int r = x / c.e2;
-      i1 = r % c.e1;
-      i0 = r / c.e1;
-    }
-    off = (long long)i0 * c.s0 + (long long)i1 * c.s1 + (long long)i2 * c.s2;
-  }
-  __device__ __forceinline__ void step(const CIdx& c, int d) {
-    if (c.e1 == 1 && c.e2 == 1) {
-      i0 += d;
-      off += (long long)d * c.s0;
-      return;
-    }
-    i2 += d;
-    if (i2 >= c.e2) {
-      const int q = i2 / c.e2;
-      i2 -= q * c.e2;
-      i1 += q;
-      if (i1 >= c.e1) {
-        const int q1 = i1 / c.e1;
-        i1 -= q1 * c.e1;
-        i0 += q1;
-      }
-    }
-    off = (long long)i0 * c.s0 + (long long)i1 * c.s1 + (long long)i2 * c.s2;
-  }
-};
 
 // The warp-per-row kernels below cut a row into pieces of ROW_PIECE elements, so that short
 // and long rows alike give enough warps to fill the GPU.
