@@ -278,10 +278,10 @@ __global__ void __launch_bounds__(NT, 2) gemm_df64_kernel(GemmArgs g) {
 
 // Matrix-vector contractions (N == 1, or M == 1 with the operands' roles swapped): bound by
 // reading the matrix once, so the GEMM tiles (15/16 of them idle on the unit dimension) are
-// the wrong shape. Each output element is one warp (lanes walk k, then a fixed shuffle tree)
-// when the matrix is contiguous along k, else one thread (k walked in order), so consecutive
-// threads read consecutive rows. Either way the sum order is fixed: results are reproducible.
-__global__ void gemv_f64_kernel(GemmArgs g, int trans, int warp_per_row) {
+// the wrong shape. One warp per output element: lanes walk k (32 loads in flight per output;
+// coalesced when the matrix is contiguous along k), then a fixed shuffle tree, so the sum
+// order is fixed and results are reproducible.
+__global__ void gemv_f64_kernel(GemmArgs g, int trans) {
   const int rows = trans ? g.N : g.M;
   const long long nout = (long long)rows * g.batch;
   // the matrix operand (indexed by row and k) and the vector operand (by k)
@@ -292,53 +292,61 @@ __global__ void gemv_f64_kernel(GemmArgs g, int trans, int warp_per_row) {
   const CIdx& mb = trans ? g.bb : g.ab;
   const CIdx& vk = trans ? g.ak : g.bk;
   const CIdx& vb = trans ? g.ab : g.bb;
-  const long long v0 = trans ? cidx(g.am, 0) : cidx(g.bn, 0);  // the vector's fixed row/column
-  const long long c0 = trans ? cidx(g.cm, 0) : cidx(g.cn, 0);
   const CIdx& cr = trans ? g.cn : g.cm;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nth = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  const long long step = warp_per_row ? nth / 32 : nth;
-  for (long long e = warp_per_row ? tid / 32 : tid; e < nout; e += step) {
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long e = w0; e < nout; e += nw) {
     const int b = (int)(e / rows), r = (int)(e - (long long)b * rows);
     const double* mrow = Mx + cidx(mb, b) + cidx(mr, r);
-    const double* vrow = Vx + cidx(vb, b) + v0;
+    const double* vrow = Vx + cidx(vb, b);  // the unit dimension's index is 0
     double s = 0.0;
     CWalk wm, wv;
-    const int k0 = warp_per_row ? lane : 0, dk = warp_per_row ? 32 : 1;
-    wm.init(mk, k0);
-    wv.init(vk, k0);
-    for (int k = k0; k < g.K; k += dk) {
+    wm.init(mk, lane);
+    wv.init(vk, lane);
+#pragma unroll 4
+    for (int k = lane; k < g.K; k += 32) {
       s = fma(mrow[wm.off], vrow[wv.off], s);
-      wm.step(mk, dk);
-      wv.step(vk, dk);
+      wm.step(mk, 32);
+      wv.step(vk, 32);
     }
-    if (warp_per_row) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane != 0) continue;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      double* c = g.C + cidx(g.cb, b) + cidx(cr, r);
+      const double val = g.alpha * s;
+      *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
     }
-    double* c = g.C + cidx(g.cb, b) + c0 + cidx(cr, r);
-    const double val = g.alpha * s;
-    *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
   }
 }
 
-// C = alpha * sum_s part[s] + beta * C, the splits added in order
+// C = alpha * sum_s part[s] + beta * C, the splits added in order. One warp per piece of
+// 256 elements of an output row: the row offset is located once and the column digits are
+// carried, not divided out per element.
 __global__ void splitk_reduce_kernel(GemmArgs g) {
-  const size_t per = (size_t)g.M * g.N;
-  const size_t tot = per * g.batch;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    int n = (int)(e % g.N);
-    size_t r = e / g.N;
-    int m = (int)(r % g.M);
-    int b = (int)(r / g.M);
-    double s = 0.0;
-    for (int q = 0; q < g.splits; ++q) s += g.part[(size_t)q * tot + e];
-    double* c = g.C + cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
-    double val = g.alpha * s;
-    if (g.beta != 0.0) val = fma(g.beta, *c, val);
-    *c = val;
+  const int lane = threadIdx.x & 31;
+  const size_t tot = (size_t)g.M * g.N * g.batch;
+  const int pieces = (g.N + 255) / 256;
+  const long long items = (long long)g.batch * g.M * pieces;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = w0; it < items; it += nw) {
+    const long long q = it / pieces;  // output row b * M + m
+    const int n0 = (int)(it - q * pieces) * 256, n1 = min(g.N, n0 + 256);
+    const int b = (int)(q / g.M), m = (int)(q - (long long)b * g.M);
+    const long long rowoff = cidx(g.cb, b) + cidx(g.cm, m);
+    const double* pr = g.part + (size_t)q * g.N;
+    CWalk cw;
+    cw.init(g.cn, n0 + lane);
+    for (int n = n0 + lane; n < n1; n += 32) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int p = 0; p < g.splits; ++p) s += pr[(size_t)p * tot + n];
+      double* c = g.C + rowoff + cw.off;
+      const double val = g.alpha * s;
+      *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
+      cw.step(g.cn, 32);
+    }
   }
 }
 
@@ -432,13 +440,10 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
       (long long)(g.N == 1 ? g.M : g.N) * g.batch >= 256) {
     const int trans = g.N == 1 ? 0 : 1;
     const long long nout = (long long)(trans ? g.N : g.M) * g.batch;
-    const CIdx& mk = trans ? g.bk : g.ak;
-    const int wpr = inner_stride(mk) == 1 ? 1 : 0;
-    const long long threads = wpr ? nout * 32 : nout;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((threads + 255) / 256, (long long)ex.sm_count * 16));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((nout * 32 + 255) / 256, (long long)ex.sm_count * 16));
     cudaEvent_t ev = nullptr;
     if (ex.timing(tag)) ex.mark_begin(&ev);
-    gemv_f64_kernel<<<blocks, 256, 0, ex.stream>>>(g, trans, wpr);
+    gemv_f64_kernel<<<blocks, 256, 0, ex.stream>>>(g, trans);
     ex.count();
     CC_CUDA(cudaGetLastError());
     if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
@@ -505,8 +510,8 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (splits > 1) {
-    size_t tot = (size_t)g.batch * g.M * g.N;
-    int blocks = (int)std::min<size_t>((tot + 255) / 256, (size_t)ex.sm_count * 8);
+    const size_t items = (size_t)g.batch * g.M * ((g.N + 255) / 256);
+    int blocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
     splitk_reduce_kernel<<<blocks, 256, 0, ex.stream>>>(g);
     ex.count();
     CC_CUDA(cudaGetLastError());

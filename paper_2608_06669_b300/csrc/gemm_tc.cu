@@ -427,6 +427,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                                  : cidx(g.cb, bz) + cidx(g.cm, my_row);
 #pragma unroll 1
       for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 32) {
+        // the rest of the tile lies past the last column, or this warp's 32 rows past the last
+        // row (both warp-uniform)
+        if (n0 + c0 >= g.N || m0 + quad * 32 >= g.M) break;
         uint32_t r[32];
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TN + c0);
         asm volatile(
