@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.h"
 
@@ -494,14 +495,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // looked up once per process (thread-safe static initialisation; retried if it threw)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     CC_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
     CC_REQUIRE(p && q == cudaDriverEntryPointSuccess, CC_ERR_CUDA, "cuTensorMapEncodeTiled not available");
-    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }();
   return fn;
 }
 
@@ -637,10 +638,14 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
       : epi == EPI_STAGED1 ? gemm_tc_kernel<BF, EPI_STAGED1>
       : epi == EPI_STAGED3 ? gemm_tc_kernel<BF, EPI_STAGED3>
                            : gemm_tc_kernel<BF, EPI_F64>;
-  static bool attr[4] = {false, false, false, false};
-  if (!attr[epi]) {
+  // the dynamic shared-memory opt-in is per device and per kernel; server threads may race here
+  static std::atomic<uint64_t> attr_done[4];
+  int dev = 0;
+  CC_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_done[epi].load() & bit)) {
     CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    attr[epi] = true;
+    attr_done[epi].fetch_or(bit);
   }
   const int grid = std::min(a.tiles, ex.sm_count);  // persistent: at most one CTA per SM
   cudaEvent_t ev = nullptr;
