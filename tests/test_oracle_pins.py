@@ -258,3 +258,20 @@ def test_fp_diis_reaches_root_of_small_workload():
     _, _, e2, hist2 = cc.solve_fp_diis(f, Bc, s.o, tol=1e-10, maxiter=100)
     assert hist2[-1] < 1e-10
     assert abs(e - e2) < 1e-10
+
+
+@pytest.mark.parametrize("gauge", ["canonical", "haar"])
+def test_residual_at_zero_amplitudes_is_the_driving_term(gauge):
+    """At t = 0 every amplitude term of the projected equations vanishes: <Phi_i^a|H|Phi_0> =
+    f_ia and <Phi_ij^ab|H|Phi_0> = (ia|jb), checked in determinant space (O0) and against the
+    integrals built directly from B. The generalised MP2 start of the solvers relies on it."""
+    o, v, naux = 2, 3, 4
+    s = synth.make_system(o, v, naux, seed=31, gauge=gauge)
+    z1, z2 = np.zeros((o, v)), np.zeros((o, o, v, v))
+    r1, r2, e = cc.residual(s.fock, s.B, o, z1, z2)
+    B = s.B
+    g = np.einsum("Pia,Pjb->ijab", B[:, :o, o:], B[:, :o, o:])
+    assert _norm(r1 - s.fock[:o, o:]) < 1e-14 and _norm(r2 - g) < 1e-14 and e == 0.0
+    h, gi = fs.integrals_from_df(s.fock, s.B, o)
+    q1, q2, _ = fs.cc_residual(h, gi, o, z1, z2)
+    assert _norm(q2 - g) < 1e-12 and _norm(q1 - s.fock[:o, o:]) < 1e-12
