@@ -118,12 +118,13 @@ const char* cc_last_error(const cc_ctx* ctx);
 size_t cc_ctx_device_bytes(const cc_ctx* ctx);
 /* Number of kernel launches the context has issued since it was created. */
 uint64_t cc_ctx_launches(const cc_ctx* ctx);
-/* Kernel timer (tracing): enable != 0 clears the records and brackets every GEMM launch
- * with CUDA events on the context's stream; enable = 0 turns it off. Tags: "ladder_build.<p>"
- * and "ladder_contract.<p>" (the two GEMMs of the particle-particle ladder, <p> = fp64, df64,
- * tf32 or bf16), and for every other contraction its index labels and kernel family, e.g.
- * "kc*Pkd>Pcd.f64" (A labels * B labels > C labels; .f64, .df64 or .tc). The time of a
- * tensor-core launch covers the GEMM and its split-k reduce, not the operand staging. */
+/* Kernel timer (tracing): enable != 0 clears the records and brackets GEMM launches with CUDA
+ * events on the context's stream; enable = 0 turns it off. enable = 1 times the two GEMMs of
+ * the particle-particle ladder, tagged "ladder_build.<p>" and "ladder_contract.<p>" (<p> =
+ * fp64, df64, tf32 or bf16); enable = 2 also times every other contraction under its index
+ * labels and the precision asked for, e.g. "kc*Pkd>Pcd.f64" (A labels * B labels > C labels;
+ * .f64, .df64 or .tc, the last also when a thin contraction ran on the FP64 kernel). The time
+ * of a tensor-core launch covers the GEMM and its split-k reduce, not the operand staging. */
 int cc_ctx_profile(cc_ctx* ctx, int enable);
 /* Launch count, summed event time (ms) and summed algorithmic flops of one tag since the
  * last cc_ctx_profile(ctx, 1). Waits for the recorded launches to finish. */

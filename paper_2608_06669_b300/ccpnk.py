@@ -167,9 +167,10 @@ class Context:
     def launches(self) -> int:
         return int(lib().cc_ctx_launches(self.h))
 
-    def profile(self, enable: bool = True):
-        """Turns the tagged kernel timer on (clearing its records) or off."""
-        _check(self.h, lib().cc_ctx_profile(self.h, int(enable)))
+    def profile(self, enable: bool = True, all_contractions: bool = False):
+        """Turns the kernel timer on (clearing its records) or off. On, it times the ladder
+        GEMMs; with all_contractions also every other contraction, under its index labels."""
+        _check(self.h, lib().cc_ctx_profile(self.h, (2 if all_contractions else 1) if enable else 0))
 
     def profile_get(self, tag: str):
         """(launches, total_ms, flops) recorded for a tag since profile(True)."""

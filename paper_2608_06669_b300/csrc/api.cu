@@ -272,6 +272,7 @@ int cc_ctx_profile(cc_ctx* ctx, int enable) {
     CC_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->prof.reset();
     ctx->prof.on = enable != 0;
+    ctx->prof.all = enable >= 2;
     return CC_OK;
   });
 }

@@ -97,6 +97,7 @@ struct Prof {
     double ms = 0.0, flops = 0.0;
   };
   bool on = false;
+  bool all = false;  // also time every untagged contraction, named by its index labels
   std::vector<Rec> pending;
   std::vector<std::pair<std::string, Sum>> done;
   void resolve();  // waits for pending events and folds them into done

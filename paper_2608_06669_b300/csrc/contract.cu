@@ -525,7 +525,7 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
               double beta, const TView& C, const char* tag, const StagedOut* so, const StagedIn* sb) {
   std::string auto_tag;  // with the timer on, an untagged contraction is named by its labels
-  if (!tag && ex.prof && ex.prof->on) {
+  if (!tag && ex.prof && ex.prof->on && ex.prof->all) {
     auto_tag = std::string(A.lab) + "*" + B.lab + ">" + C.lab +
                (prec == CC_FP64 ? ".f64" : prec == CC_DF64 ? ".df64" : ".tc");
     tag = auto_tag.c_str();

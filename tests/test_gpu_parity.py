@@ -256,3 +256,23 @@ def test_pnk_fp64_workload(ctx):
     t1, t2, rep = gpu_system(ctx, s).solve("pnk", "fp64")
     assert rep["status_code"] == 0, rep
     assert abs(rep["energy"] - ref) < 1e-8
+
+
+def test_kernel_timer_levels(ctx):
+    """Level 1 times only the ladder GEMMs; level 2 also names every other contraction by its
+    index labels. Timing does not change the result."""
+    s = synth.make_system(3, 9, 10, seed=21, gauge="haar")
+    g = gpu_system(ctx, s)
+    t1, t2 = synth.random_amplitudes(np.random.default_rng(2), 3, 9, 0.1, 0.1)
+    r1, r2, e = g.residual(t1, t2)
+    ctx.profile(True)
+    g.residual(t1, t2)
+    lvl1 = ctx.profile_list()
+    ctx.profile(True, all_contractions=True)
+    q1, q2, eq = g.residual(t1, t2)
+    lvl2 = ctx.profile_list()
+    ctx.profile(False)
+    assert set(lvl1) == {"ladder_build.fp64", "ladder_contract.fp64"}
+    assert set(lvl1) < set(lvl2) and any(k.endswith(".f64") and ">" in k for k in lvl2)
+    assert all(n >= 1 and ms >= 0.0 for n, ms, _ in lvl2.values())
+    assert np.array_equal(r2, q2) and np.array_equal(r1, q1) and e == eq
