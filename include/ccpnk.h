@@ -151,17 +151,23 @@ int cc_residual(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
 int cc_jvp(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
            const double* d1, const double* d2, double* j1, double* j2, cc_precision prec);
 
-/* y = A_F x (inverse = 0) or y = A_F^{-1} x (inverse = 1), where
+/* y = A_F x (inverse = 0) or y = A_F^{-1} x (inverse = 1 or 2), where
  * (A_F x)_ij^ab = sum_c (f_ac x_ij^cb + f_bc x_ij^ac) - sum_k (f_ki x_kj^ab + f_kj x_ik^ab) and
  * (A_F x)_i^a = sum_c f_ac x_i^c - sum_k f_ki x_k^a (Eq. Preconditioner, App. C; the factor 4
- * printed there comes from an unnormalised projection and is not applied). The inverse is the
- * inner GMRES of the solver (relative tolerance 1e-12 in FP64). */
+ * printed there comes from an unnormalised projection and is not applied). inverse = 1 is the
+ * inner GMRES of the solver (relative tolerance 1e-12 in FP64, 1e-6 otherwise); inverse = 2 is
+ * exact: rotate into the eigenbases of the occupied and virtual Fock blocks, divide by
+ * e_a + e_b - e_i - e_j (e_a - e_i for singles) and rotate back, the rotations at prec and,
+ * for the tensor-core precisions, the doubles projected back onto y_ij^ab = y_ji^ba. */
 int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2,
                 double* y1, double* y2, int inverse, cc_precision prec);
 
 /* Solves R(t) = 0. t1/t2: on input the initial guess if use_guess != 0 (otherwise the
- * generalised MP2 start t1 = 0, t2 = A_F^{-1}(-R2(0)) is used); on output the solution.
- * Returns CC_OK, CC_ERR_NOT_CONVERGED or CC_ERR_DIVERGED with the report filled. */
+ * generalised MP2 start t1 = 0, t2 = A_F^{-1}(-R2(0)) is used, with R2(0)_ij^ab = (ia|jb)); on
+ * output the solution. With a tensor-core precision the JVPs and A_F^{-1} run on tensor cores
+ * and every A_F^{-1} output is projected onto t_ij^ab = t_ji^ba before it enters the Krylov
+ * space; the residual, energy, update and orthogonalisation stay FP64 (or double-float, by
+ * outer_prec). Returns CC_OK, CC_ERR_NOT_CONVERGED or CC_ERR_DIVERGED with the report filled. */
 int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2,
              int use_guess, cc_report* report);
 
