@@ -65,3 +65,25 @@ def test_default_options_follow_the_paper():
     o = ccpnk.default_opts("pnk", "fp64")
     assert o.gamma == 0.9 and o.alpha == 1.5 and o.tol == 1e-8 and o.eta_max == 0.9
     assert o.method == 2 and o.prec == 0 and o.m_max == 30
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-12), ("df64", 1e-12), ("tf32", 1e-6), ("tf32x3", 1e-8),
+                                       ("bf16x3", 1e-7)])
+def test_inner_tolerance_follows_the_precision(prec, rtol):
+    """The inner A_F GMRES asks for no more than the precision of its operator delivers."""
+    from paper_2608_06669_b300 import ccpnk
+
+    o = ccpnk.default_opts("pnk", prec)
+    assert o.inner_rtol == rtol and o.inner_max == 50 and o.af_direct == 0
+    assert ccpnk.PREC[prec] == o.prec
+
+
+def test_precision_codes_match_the_header():
+    from paper_2608_06669_b300 import ccpnk
+
+    text = open(HEADER).read()
+    codes = dict(re.findall(r"(CC_(?:FP64|MIXED_TF32|MIXED_BF16X3|MIXED_TF32X3|DF64))\s*=\s*(\d+)", text))
+    assert {k: int(v) for k, v in codes.items()} == {"CC_FP64": ccpnk.PREC["fp64"], "CC_MIXED_TF32": ccpnk.PREC["tf32"],
+                                                     "CC_MIXED_BF16X3": ccpnk.PREC["bf16x3"],
+                                                     "CC_MIXED_TF32X3": ccpnk.PREC["tf32x3"],
+                                                     "CC_DF64": ccpnk.PREC["df64"]}
