@@ -59,6 +59,11 @@ void system_init(const Exec& ex, System& s, int o, int v, int P, const double* f
   k_make_L_ovov(ex, o, v, s.Govov.p, s.Lovov.p);
 }
 
+size_t stage_cache_cap(int o, int v, int P) {
+  const double big = (double)P * v * v + (double)o * o * v * v;
+  return (size_t)std::min(1073741824.0, 32.0 * 4.0 * big);
+}
+
 int ladder_block_for(int v) {
   const double cap = 2.0 * 1024 * 1024 * 1024;
   const double per_a = 8.0 * (double)v * v * v;
@@ -86,6 +91,8 @@ Engine::Engine(const Exec& ex, const System& s) : ex_(ex), s_(s) {
   alloc(X_, oovv);
   alloc(Y2_, oovv);
   ladder_block_ = ladder_block_for(v);
+  stage_.cap = stage_cache_cap(o, v, P);
+  if (ex.pool->budget()) stage_.cap = std::min(stage_.cap, ex.pool->budget() / 8);
   W_.alloc(ex.pool, (size_t)ladder_block_ * v * v * v);
   // the tangent's stacked factors [dBt_vv ; Bt_vv] and [Bt_vv ; dBt_vv]
   XsYs_.alloc(ex.pool, 4 * (size_t)P * v * v);
@@ -107,7 +114,8 @@ struct TP {
 
 }  // namespace
 
-void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* T, double* R, cc_precision prec) {
+void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* T, double* R, cc_precision prec,
+                    bool fixed_xy, bool fixed_t) {
   // R[i][j][a][b] += L[i][j][a][b] = sum_{P,c,d} X[P][a][c] Y[P][b][d] T[i][j][c][d].
   // The caller guarantees that V_{ac,bd} = sum_P X[P][a][c] Y[P][b][d] is symmetric under
   // (a,c) <-> (b,d); with T[i][j][c][d] = T[j][i][d][c] that makes L[i][j][a][b] = L[j][i][b][a].
@@ -190,9 +198,9 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
     // W2[(a,b)][s * kpad + c v + d]: the strides below count floats of W2
     StagedOut so{W2, kpad, nseg, nseg == 3 ? 0b010 : 0};
     TView Ws = view_strided(nullptr, "abcd", {al, bl, v, v}, {(long long)bl * kk, kk, v, 1});
-    contract(ex_, prec, 1.0, Xa, Yb, 0.0, Ws, tb, &so, nullptr);
+    contract(ex_, prec, 1.0, Xa, Yb, 0.0, Ws, tb, &so, nullptr, &stage_, fixed_xy ? 3 : 0);
     StagedIn sb{W2, rows_pad, (int)kk};
-    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc, nullptr, &sb);
+    contract(ex_, prec, 1.0, view(Tm, "ijcd", {o, o, v, v}), W, 0.0, Lv, tc, nullptr, &sb, &stage_, fixed_t ? 1 : 0);
   }
   k_ladder_mirror_add(ex_, o, v, blk, L, R);
 }
@@ -238,7 +246,8 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
     r.dyn = true;
     return r;
   };
-  // C = alpha A B + beta C, linearised in tangent mode
+  // C = alpha A B + beta C, linearised in tangent mode. There the value-side factor is fixed
+  // until the next value() call, so its tensor-core staging may be kept across JVPs.
   auto bil = [&](double alpha, const TP& A, const TP& B, double beta, const TP& C) {
     if (!tan) {
       contract(ex, prec, alpha, A.v, B.v, beta, C.v);
@@ -246,11 +255,11 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
     }
     double b = beta;
     if (A.dyn) {
-      contract(ex, prec, alpha, A.t, B.v, b, C.t);
+      contract(ex, prec, alpha, A.t, B.v, b, C.t, nullptr, nullptr, nullptr, &stage_, 2);
       b = 1.0;
     }
     if (B.dyn) {
-      contract(ex, prec, alpha, A.v, B.t, b, C.t);
+      contract(ex, prec, alpha, A.v, B.t, b, C.t, nullptr, nullptr, nullptr, &stage_, 1);
       b = 1.0;
     }
   };
@@ -323,7 +332,7 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
   } else {
     // d[(ac|bd)~ t] = (ac|bd)~ dt + sum_P (dBt_ac Bt_bd + Bt_ac dBt_bd) t; the second factor
     // pair, stacked along the auxiliary index, is again symmetric under (a,c) <-> (b,d)
-    ladder(Btvv_.val.p, Btvv_.val.p, P, t_.tan.p + ov, r2, prec);
+    ladder(Btvv_.val.p, Btvv_.val.p, P, t_.tan.p + ov, r2, prec, true, false);
     const size_t pvv = (size_t)P * v * v;
     double* Xs = XsYs_.p;
     double* Ys = XsYs_.p + 2 * pvv;
@@ -331,7 +340,7 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
     k_copy(ex, pvv, Btvv_.val.p, Xs + pvv);
     k_copy(ex, pvv, Btvv_.val.p, Ys);
     k_copy(ex, pvv, Btvv_.tan.p, Ys + pvv);
-    ladder(Xs, Ys, 2 * P, t_.val.p + ov, r2, prec);
+    ladder(Xs, Ys, 2 * P, t_.val.p + ov, r2, prec, false, true);
   }
   // hole ladder with its quadratic part: W_klij = (ki|lj)~ + sum_cd (kc|ld) t_ij^cd
   TP Woo = dyn(Woo_, 0, "klij", {o, o, o, o});
@@ -366,6 +375,7 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
 
 void Engine::value(const double* t, double* r, double* energy_dev, cc_precision prec) {
   const int o = s_.o, v = s_.v, n = s_.n;
+  stage_.clear();  // the values change: staged copies of the old ones are stale
   if (t != t_.val.p) k_copy(ex_, s_.namp(), t, t_.val.p);
   program(false, prec, r);
   if (energy_dev)

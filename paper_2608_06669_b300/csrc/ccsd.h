@@ -28,6 +28,10 @@ void system_init(const Exec& ex, System& s, int o, int v, int P, const double* f
 // (a, b, c, d) slab of at most 2 GiB; larger blocks give the tensor-core GEMMs more tiles.
 int ladder_block_for(int v);
 
+// Bytes the tangent program may keep in staged copies of its value-side operands: room for
+// about 32 staged copies (4-byte words) of the largest tensors, at most 1 GiB.
+size_t stage_cache_cap(int o, int v, int P);
+
 // Intermediates of one residual evaluation; the tangent program reuses the values.
 class Engine {
  public:
@@ -46,7 +50,9 @@ class Engine {
     DBuf<double> val, tan;
   };
   void alloc(Pair& x, size_t n);
-  void ladder(const double* Xv, const double* Yv, int Paux, const double* T, double* R, cc_precision prec);
+  // fixed_xy / fixed_t: X, Y / T stay fixed until the next value() (their staging may be kept)
+  void ladder(const double* Xv, const double* Yv, int Paux, const double* T, double* R, cc_precision prec,
+              bool fixed_xy = false, bool fixed_t = false);
   void program(bool tan, cc_precision prec, double* r_out);
   Exec ex_;
   const System& s_;
@@ -57,6 +63,7 @@ class Engine {
   DBuf<double> XsYs_;     // stacked factors of the tangent ladder
   DBuf<double> W2_;       // tensor-core ladder slab in staging layout (TF32 or BF16 words)
   int w2_mode_ = -1;      // precision whose layout W2_ holds
+  StageCache stage_;      // staged value-side operands of the tangent program (cleared by value())
   DBuf<double> scratch_;  // reduction partials
 };
 

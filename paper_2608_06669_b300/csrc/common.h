@@ -183,6 +183,29 @@ struct StagedIn {  // the B operand already staged (rows padded to the tile, zer
   int rows_pad, kk;  // kk = nseg * kpad elements per row
 };
 
+// Tensor-core staging copies of operands that stay fixed across calls: in the tangent program
+// the value-side operands do not change between the JVPs of one Newton step, so their staged
+// copies are kept (up to cap bytes) instead of being gathered again for every JVP. An Engine
+// owns one and clears it whenever its values change.
+struct StageKey {
+  const double* src;
+  CIdx rix, kix, bix;
+  int rows, K, batch, rows_pad, k_pad, nseg, seg_lo, bf;
+};
+bool operator==(const StageKey& a, const StageKey& b);
+struct StageCache {
+  struct Ent {
+    StageKey key;
+    DBuf<double> buf;
+  };
+  std::vector<Ent> ents;
+  size_t bytes = 0, cap = 0;
+  void clear() {
+    ents.clear();
+    bytes = 0;
+  }
+};
+
 struct GemmArgs {
   const double* A;
   const double* B;
@@ -198,6 +221,8 @@ struct GemmArgs {
   double* part;          // split-K partials [splits][batch][M][N]
   const StagedOut* so;   // tensor-core only: C in staging layout
   const StagedIn* sb;    // tensor-core only: B already staged
+  StageCache* cache;     // tensor-core only: where fixed operands' staged copies are kept
+  int cache_mask;        // bit 0: A is fixed across calls (cacheable), bit 1: B
 };
 
 // Tensor-core GEMM (gemm_tc.cu): same contract as the FP64 kernel, run on tcgen05.
@@ -226,9 +251,11 @@ TView view_strided(double* p, const char* labels, std::initializer_list<int> ext
 // C = alpha * contract(A, B) + beta * C over the labels: labels of C present in both A and B
 // are batch modes, labels in A and C the row modes, in B and C the column modes, labels in
 // A and B only are summed. prec selects the FP64 FMA kernel or the tensor-core kernel.
+// cache / cache_mask: operands (bit 0 for A, bit 1 for B) whose contents stay fixed until the
+// cache is cleared may have their tensor-core staging kept there.
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
               double beta, const TView& C, const char* tag = nullptr, const StagedOut* so = nullptr,
-              const StagedIn* sb = nullptr);
+              const StagedIn* sb = nullptr, StageCache* cache = nullptr, int cache_mask = 0);
 
 // ---------------------------------------------------------------------------
 // kernels with host launchers (elementwise.cu)

@@ -522,8 +522,19 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
 
 }  // namespace
 
+static bool same_cidx(const CIdx& a, const CIdx& b) {
+  return a.e1 == b.e1 && a.e2 == b.e2 && a.s0 == b.s0 && a.s1 == b.s1 && a.s2 == b.s2;
+}
+
+bool operator==(const StageKey& a, const StageKey& b) {
+  return a.src == b.src && same_cidx(a.rix, b.rix) && same_cidx(a.kix, b.kix) && same_cidx(a.bix, b.bix) &&
+         a.rows == b.rows && a.K == b.K && a.batch == b.batch && a.rows_pad == b.rows_pad && a.k_pad == b.k_pad &&
+         a.nseg == b.nseg && a.seg_lo == b.seg_lo && a.bf == b.bf;
+}
+
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
-              double beta, const TView& C, const char* tag, const StagedOut* so, const StagedIn* sb) {
+              double beta, const TView& C, const char* tag, const StagedOut* so, const StagedIn* sb,
+              StageCache* cache, int cache_mask) {
   std::string auto_tag;  // with the timer on, an untagged contraction is named by its labels
   if (!tag && ex.prof && ex.prof->on && ex.prof->all) {
     auto_tag = std::string(A.lab) + "*" + B.lab + ">" + C.lab +
@@ -607,6 +618,8 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
   g.splits = 1;
   g.so = so;
   g.sb = sb;
+  g.cache = cache;
+  g.cache_mask = cache ? cache_mask : 0;
   g.a_kfast = gk.empty() ? 1 : (inner_stride(g.ak) == 1);
   g.b_kfast = gk.empty() ? 1 : (inner_stride(g.bk) == 1 && inner_stride(g.bn) != 1);
 

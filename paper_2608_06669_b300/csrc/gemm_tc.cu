@@ -535,18 +535,43 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   // the split precisions stage [hi|hi|lo] against [hi|lo|hi] along a three times longer k
   const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
   const int kk = nseg * k_pad;
-  const size_t nA = (size_t)g.batch * rowsA * kk, nB = g.sb ? 0 : (size_t)g.batch * rowsB * kk;
-  DBuf<double> stA(ex.pool, (nA * sizeof(T) + 7) / 8), stB(ex.pool, (nB * sizeof(T) + 7) / 8);
-  T* fA = reinterpret_cast<T*>(stA.p);
-  T* fB = reinterpret_cast<T*>(stB.p);
   // warp-per-row-piece kernels: eight pieces per 256-thread block and pass
   auto blocks_for_rows = [&](size_t rows, size_t row_len) {
     const size_t items = rows * ((row_len + ROW_PIECE - 1) / ROW_PIECE);
     return (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
   };
-  gather_kernel<T><<<blocks_for_rows((size_t)g.batch * rowsA, k_pad), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K, g.batch, rowsA, k_pad, nseg,
-                                                           nseg == 3 ? 0b100 : 0, fA);
-  ex.count();
+  // Staged copy of one operand: taken from the cache when the caller marked the operand as
+  // fixed and it was staged before with the same layout, else gathered (into the cache when
+  // it is marked and fits, into a temporary otherwise).
+  auto stage = [&](int which, const double* src, const CIdx& rix, const CIdx& kix, const CIdx& bix, int rows,
+                   int rows_pad, int seg_lo, DBuf<double>& tmp) -> T* {
+    const size_t dbl = ((size_t)g.batch * rows_pad * kk * sizeof(T) + 7) / 8;
+    double* dst = nullptr;
+    if (g.cache && (g.cache_mask & which)) {
+      const StageKey key{src, rix, kix, bix, rows, g.K, g.batch, rows_pad, k_pad, nseg, seg_lo, BF ? 1 : 0};
+      for (auto& e : g.cache->ents)
+        if (e.key == key) return reinterpret_cast<T*>(e.buf.p);
+      if (g.cache->bytes + dbl * 8 <= g.cache->cap) {
+        g.cache->ents.emplace_back();
+        StageCache::Ent& e = g.cache->ents.back();
+        e.key = key;
+        e.buf.alloc(ex.pool, dbl);
+        g.cache->bytes += dbl * 8;
+        dst = e.buf.p;
+      }
+    }
+    if (!dst) {
+      tmp.alloc(ex.pool, dbl);
+      dst = tmp.p;
+    }
+    gather_kernel<T><<<blocks_for_rows((size_t)g.batch * rows_pad, k_pad), 256, 0, ex.stream>>>(
+        src, rix, kix, bix, rows, g.K, g.batch, rows_pad, k_pad, nseg, seg_lo, reinterpret_cast<T*>(dst));
+    ex.count();
+    return reinterpret_cast<T*>(dst);
+  };
+  DBuf<double> stA, stB;
+  T* fA = stage(1, g.A, g.am, g.ak, g.ab, g.M, rowsA, nseg == 3 ? 0b100 : 0, stA);
+  T* fB = nullptr;
   int rowsBmap = rowsB;
   if (g.sb) {
     // B was written in staging layout by an earlier contraction
@@ -555,9 +580,7 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
     fB = static_cast<T*>(const_cast<void*>(g.sb->base));
     rowsBmap = g.sb->rows_pad;
   } else {
-    gather_kernel<T><<<blocks_for_rows((size_t)g.batch * rowsB, k_pad), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K, g.batch, rowsB, k_pad,
-                                                             nseg, nseg == 3 ? 0b010 : 0, fB);
-    ex.count();
+    fB = stage(2, g.B, g.bn, g.bk, g.bb, g.N, rowsB, nseg == 3 ? 0b010 : 0, stB);
   }
   CC_CUDA(cudaGetLastError());
   CC_REQUIRE(!g.so || g.beta == 0.0, CC_ERR_INVALID, "a staged output cannot accumulate");
