@@ -167,7 +167,10 @@ int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2,
  * output the solution. With a tensor-core precision the JVPs and A_F^{-1} run on tensor cores
  * and every A_F^{-1} output is projected onto t_ij^ab = t_ji^ba before it enters the Krylov
  * space; the residual, energy, update and orthogonalisation stay FP64 (or double-float, by
- * outer_prec). Returns CC_OK, CC_ERR_NOT_CONVERGED or CC_ERR_DIVERGED with the report filled. */
+ * outer_prec). Between two residual evaluations the JVPs keep the tensor-core staging of the
+ * operands that do not change (at most about 32 copies of the largest tensors, 1 GiB, or an
+ * eighth of the context's budget), so a mixed solve holds that much more device memory.
+ * Returns CC_OK, CC_ERR_NOT_CONVERGED or CC_ERR_DIVERGED with the report filled. */
 int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2,
              int use_guess, cc_report* report);
 
