@@ -100,64 +100,114 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds_budget=15.0):
-    """The oracle as it stands, on the host cores: mean time of one FP64 residual evaluation
-    on this workload, times the residual evaluations the oracle's reference solver needs to
-    reach the root (tests/golden/energies.json)."""
-    from oracle import dfccsd as cc
-    from paper_2608_06669_b300 import synth
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
+
+def oracle_threads():
     try:
         from threadpoolctl import threadpool_info
 
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [os.cpu_count()])
+        return max([i.get("num_threads", 1) for i in threadpool_info()] or [os.cpu_count()])
     except Exception:
-        cores = os.cpu_count()
-    s = synth.workload(WORKLOAD)
-    t1, t2 = cc.mp2_guess(s.fock, s.B, s.o)
+        return os.cpu_count()
+
+
+def oracle_solve_iterations():
+    """Residual evaluations the oracle's FP+DIIS solve of the bench workload takes to converge,
+    from a complete oracle run (tests/golden/make_golden.py)."""
+    with open(os.path.join(ROOT, "tests", "golden", "energies.json")) as fh:
+        return json.load(fh)[WORKLOAD]["iterations"]
+
+
+class OracleSolve:
+    """The oracle's own FP+DIIS solve of the bench workload from the MP2 start, run one
+    iteration (a residual evaluation, the update and the DIIS extrapolation) at a time."""
+
+    def __init__(self):
+        from oracle import dfccsd as cc
+        from paper_2608_06669_b300 import synth
+
+        s = synth.workload(WORKLOAD)
+        f, Bc, _ = cc.to_eigenbasis(s.fock, s.B, s.o)
+        t0 = time.perf_counter()
+        self.steps = cc.fp_diis_iterates(f, Bc, s.o, diis_size=12)
+        self.start_s = time.perf_counter() - t0
+        self.done = 0
+        self.last_res = None
+
+    def run(self, n):
+        """n iterations; returns their wall time in seconds."""
+        t0 = time.perf_counter()
+        for _ in range(n):
+            _, _, _, _, self.last_res = next(self.steps)
+            self.done += 1
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(seconds_budget=12.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the bench workload:
+    iterations of its own FP+DIIS solve from the MP2 start on every thread the BLAS runs (about
+    seconds_budget of work), and one iteration with one thread. The metric is time to
+    solution, so the sample's seconds per iteration are scaled by the iterations the complete
+    oracle solve takes (tests/golden/energies.json)."""
+    from threadpoolctl import threadpool_limits
+
+    evals = oracle_solve_iterations()
+    cores = oracle_threads()
+    sol = OracleSolve()
     times = []
     t_start = time.perf_counter()
     while time.perf_counter() - t_start < seconds_budget or len(times) < 2:
-        t0 = time.perf_counter()
-        cc.residual(s.fock, s.B, s.o, t1, t2)
-        times.append(time.perf_counter() - t0)
-        if len(times) >= 20:
-            break
-    with open(os.path.join(ROOT, "tests", "golden", "energies.json")) as fh:
-        evals = json.load(fh)[WORKLOAD]["iterations"]
-    per = statistics.mean(times)
-    return {"value": per * evals, "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(times)} oracle FP64 residual evaluations at o=10 v=90 naux=300 "
-                      f"({per:.3f} s each) x {evals} evaluations of the oracle FP+DIIS solve"}
+        times.append(sol.run(1))
+    per = statistics.mean(times[1:]) if len(times) > 2 else statistics.mean(times)
+    with threadpool_limits(limits=1):
+        per1 = sol.run(1)
+    return {"value": per * evals, "unit": "s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "s_per_iteration": per, "s_per_iteration_1_thread": per1, "iterations_to_solution": evals,
+            "value_1_thread": per1 * evals,
+            "sample": f"{len(times)} + 1 iterations of the oracle's FP+DIIS solve of o=10 v=90 naux=300 from the "
+                      f"MP2 start ({per:.3f} s each on {cores} threads, {per1:.3f} s on 1 thread; the complete "
+                      f"solve takes {evals} iterations, so value = s/iteration x {evals}); ||R|| after "
+                      f"{sol.done} iterations {sol.last_res:.2e}"}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle's own FP+DIIS solve of the bench workload. Each step
+    runs a bounded sample of that one solve (--ref-iterations iterations, continuing where the
+    previous step stopped, warm-up steps included), so ms_per_step is the measured time of a
+    step; value is the time to solution, the measured seconds per iteration times the
+    iterations the complete oracle solve takes."""
     rank, _, world = rank_info()
     if rank != 0:
         return
-    base = cpu_baseline(seconds_budget=5.0)
-    from oracle import dfccsd as cc
-    from paper_2608_06669_b300 import synth
-
-    s = synth.workload(WORKLOAD)
-    t1, t2 = cc.mp2_guess(s.fock, s.B, s.o)
-    with open(os.path.join(ROOT, "tests", "golden", "energies.json")) as fh:
-        evals = json.load(fh)[WORKLOAD]["iterations"]
+    evals = oracle_solve_iterations()
+    cores = oracle_threads()
+    sol = OracleSolve()
     for _ in range(args.warmup):
-        cc.residual(s.fock, s.B, s.o, t1, t2)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        cc.residual(s.fock, s.B, s.o, t1, t2)
-        times.append((time.perf_counter() - t0) * evals)
-    val = statistics.mean(times)
+        sol.run(args.ref_iterations)
+    steps = [sol.run(args.ref_iterations) for _ in range(args.steps)]
+    per_step = statistics.mean(steps)
+    per_it = per_step / args.ref_iterations
+    val = per_it * evals
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "o": 10, "v": 90, "naux": 300, "gauge": "rotated",
-                       "tol": 1e-8, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": val, "unit": "s", "cores": base["cores"], "kind": "oracle",
-                             "sample": f"each step: one oracle FP64 residual evaluation x {evals} evaluations"},
+                       "tol": 1e-8, "l2": "n/a (CPU)",
+                       "step": f"{args.ref_iterations} iterations of the oracle FP+DIIS solve (value: time to "
+                               f"solution = s/iteration x {evals})"},
+            "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": f"{(args.warmup + args.steps) * args.ref_iterations} iterations of one oracle "
+                                       f"FP+DIIS solve from the MP2 start, {per_it:.3f} s each; ||R|| {sol.last_res:.2e} "
+                                       f"after {sol.done}; the complete solve takes {evals}"},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -428,6 +478,39 @@ def run_kernels(args):
                           **extra, **{k: rep[k] for k in keep}}), flush=True)
 
 
+def run_peaks(args):
+    """Measured arithmetic rates on this GPU: the FP64 and FP32 FMA pipes (the library's FMA-chain
+    probe) and torch's FP64, TF32 and BF16 matmuls (best of five, CUDA events)."""
+    import torch
+
+    from paper_2608_06669_b300 import ccpnk
+
+    out = {"mode": "peaks", "fp64_fma_tflops": ccpnk.probe_fma_rate(0, True),
+           "fp32_fma_tflops": ccpnk.probe_fma_rate(0, False),
+           "fp64_fma_nominal_tflops": FP64_PEAK_TFLOPS}
+
+    def mm(dtype, n, tf32=False):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        best = 1e30
+        for rep in range(6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep:
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        return 2.0 * n ** 3 / best / 1e12
+
+    out["torch_fp64_matmul_4096_tflops"] = mm(torch.float64, 4096)
+    out["torch_tf32_matmul_8192_tflops"] = mm(torch.float32, 8192, tf32=True)
+    out["torch_bf16_matmul_8192_tflops"] = mm(torch.bfloat16, 8192)
+    print(json.dumps(out), flush=True)
+
+
 def run_case(args):
     """One residual or JVP evaluation on a named workload or an (o, v, naux) system: the small,
     single-call cases that kernel profiles are taken on."""
@@ -468,6 +551,7 @@ def main():
     ap.add_argument("--case", default="", help="one evaluation on a workload name or 'o,v,naux' instead")
     ap.add_argument("--case-op", default="jvp", choices=["jvp", "residual"])
     ap.add_argument("--case-prec", default="tf32x3", choices=["fp64", "tf32", "tf32x3", "bf16x3", "df64"])
+    ap.add_argument("--peaks", action="store_true", help="measure the FMA-pipe and matmul rates instead")
     ap.add_argument("--kernels", default="", help="per-kernel rates and capped solves on this workload instead")
     ap.add_argument("--shift", type=float, default=0.2, help="FP+DIIS level shift in --kernels")
     ap.add_argument("--no-fp64-solve", action="store_true")
@@ -484,9 +568,12 @@ def main():
     ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "bf16x3", "tf32", "fp64"])
     ap.add_argument("--af-gmres", action="store_true", help="invert A_F by inner GMRES in the timed solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ref-iterations", type=int, default=3, help="oracle iterations per reference step")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.peaks:
+        run_peaks(args)
     elif args.serve:
         run_serve(args)
     elif args.kernels:

@@ -47,6 +47,7 @@ extern "C" {
 #define CC_ERR_DIVERGED (-4)     /* non-finite or exploding residual */
 #define CC_ERR_CUDA (-5)         /* a CUDA runtime error */
 #define CC_ERR_TIMEOUT (-6)      /* a bounded device-side wait gave up */
+#define CC_ERR_CANCELLED (-7)    /* cc_serve_cancel stopped the request; the report is filled */
 
 typedef enum {
   CC_FP64 = 0,          /* every contraction in FP64 (FMA pipe) */
@@ -102,7 +103,7 @@ typedef struct {
   int jvps;              /* Jacobian-vector products */
   int af_applies;        /* applications of A_F (inside inner solves) or of A_F^{-1} (direct) */
   int krylov_iters;      /* total outer Arnoldi steps */
-  int status;            /* CC_OK, CC_ERR_NOT_CONVERGED or CC_ERR_DIVERGED */
+  int status;            /* CC_OK, CC_ERR_NOT_CONVERGED, CC_ERR_DIVERGED or CC_ERR_CANCELLED */
   double seconds;        /* wall time of the solve */
 } cc_report;
 
@@ -114,6 +115,28 @@ void cc_solve_opts_default(cc_solve_opts* opts, cc_method method, cc_precision p
 int cc_ctx_create(cc_ctx** ctx, int device, size_t mem_budget, void* stream);
 void cc_ctx_destroy(cc_ctx* ctx);
 const char* cc_last_error(const cc_ctx* ctx);
+/* Options of a context (tuning and testing knobs of this library; the paper has no counterpart).
+ * CC_OPT_STAGE_CACHE_BYTES: bytes the JVPs of a solve may keep in tensor-core staged copies of
+ *   operands that stay fixed between two residual evaluations (default: room for about 32 copies
+ *   of the largest tensors, at most 1 GiB or an eighth of the budget; 0 turns the cache off;
+ *   -1 restores the default). Results do not depend on it, only the time does.
+ * CC_OPT_WAIT_LIMIT_NS: bound, in nanoseconds of the GPU's global timer, on every wait of a
+ *   device-side pipeline (default 4e9, at least 1e5); a wait that gives up makes the call
+ *   return CC_ERR_TIMEOUT and leaves the context usable.
+ * Returns CC_OK or CC_ERR_INVALID (unknown option, value out of range). */
+#define CC_OPT_STAGE_CACHE_BYTES 1
+#define CC_OPT_WAIT_LIMIT_NS 2
+int cc_ctx_set_option(cc_ctx* ctx, int option, long long value);
+/* Self-test of the bounded device waits: runs one kernel whose wait on an mbarrier that nothing
+ * arrives at gives up after CC_OPT_WAIT_LIMIT_NS, so the call returns CC_ERR_TIMEOUT; the
+ * kernel returns normally and the context stays usable. A diagnostic of this library. */
+int cc_ctx_selftest_wait(cc_ctx* ctx);
+/* Measured FMA throughput of the device (a diagnostic of this library): fp64 = 1 the FP64 pipe,
+ * 0 the FP32 pipe, in TFLOP/s (2 flops per FMA) from the fastest of three timed launches of a
+ * kernel running eight independent FMA chains per thread on every SM. It is the measured
+ * counterpart of the FMA-pipe peaks the rooflines divide by. Allocates and frees its own
+ * output buffer. Returns CC_OK, CC_ERR_INVALID or CC_ERR_CUDA. */
+int cc_probe_fma_rate(int device, int fp64, double* tflops);
 /* Device bytes currently held by the context's pools. */
 size_t cc_ctx_device_bytes(const cc_ctx* ctx);
 /* Number of kernel launches the context has issued since it was created. */
@@ -151,6 +174,13 @@ int cc_residual(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
 int cc_jvp(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
            const double* d1, const double* d2, double* j1, double* j2, cc_precision prec);
 
+/* J(t) d_k for ndir directions at one point t, with one residual evaluation at t (App. B): the
+ * values of the intermediates are kept and each direction runs the tangent program, which keeps
+ * the tensor-core staging of its fixed operands across the directions. d1s / d2s / j1s / j2s
+ * hold ndir vectors back to back ([ndir][o][v] and [ndir][o][o][v][v]); host or device. */
+int cc_jvp_multi(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2, int ndir, const double* d1s,
+                 const double* d2s, double* j1s, double* j2s, cc_precision prec);
+
 /* y = A_F x (inverse = 0) or y = A_F^{-1} x (inverse = 1 or 2), where
  * (A_F x)_ij^ab = sum_c (f_ac x_ij^cb + f_bc x_ij^ac) - sum_k (f_ki x_kj^ab + f_kj x_ik^ab) and
  * (A_F x)_i^a = sum_c f_ac x_i^c - sum_k f_ki x_k^a (Eq. Preconditioner, App. C; the factor 4
@@ -184,9 +214,11 @@ int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, do
  * Scratch: up to 1024 partial sums in a fixed device array inside the library (8 KB per GPU
  * that loads it, held until exit); a launch that would need more partial sums is rejected
  * with CC_ERR_INVALID. Every call shares that array, so calls that overlap on the GPU (on
- * different streams, or from different threads) race; order them on one stream. The first
- * call on a device looks up the array's device address; make that first call before any
- * stream capture. Returns CC_OK, CC_ERR_INVALID (NULL pointer, bad sizes) or CC_ERR_CUDA. */
+ * different streams, or from different threads) race; order them on one stream. cc_sys_create
+ * readies this entry point: it loads the module that holds the array and the energy kernels
+ * (lazy module loading would otherwise allocate inside the driver on the first call) and looks
+ * up the array's device address, so the calls themselves load and allocate nothing.
+ * Returns CC_OK, CC_ERR_INVALID (NULL pointer, bad sizes) or CC_ERR_CUDA. */
 int cc_energy_noalloc(const cc_sys* sys, const double* t1, const double* t2, double* energy, void* stream);
 
 /* Continuous-batching server on one device (the serving pattern of the solver; the paper
@@ -205,6 +237,10 @@ int cc_serve_submit(cc_server* srv, int o, int v, int naux, const double* fock, 
  * the solution copied to t1/t2 (host, may be NULL). That call releases the amplitudes; the
  * ticket's times stay available through cc_serve_times. */
 int cc_serve_poll(cc_server* srv, uint64_t ticket, cc_report* report, double* t1, double* t2);
+/* Cancels a request: one still waiting is dropped, one running stops at its next outer
+ * iteration. Its poll then returns CC_ERR_CANCELLED with the report of what ran (a waiting one:
+ * zeros) and the amplitudes reached so far. CC_ERR_INVALID for an unknown or released ticket. */
+int cc_serve_cancel(cc_server* srv, uint64_t ticket);
 /* Timestamps of a request in seconds since server creation: submit, admit, finish (CC_PENDING
  * until it has finished). */
 int cc_serve_times(cc_server* srv, uint64_t ticket, double* t_submit, double* t_admit, double* t_finish);

@@ -184,23 +184,21 @@ def solve_AF(fock: np.ndarray, o: int, b1: np.ndarray, b2: np.ndarray, shift: fl
 
 
 def mp2_guess(fock, B, o):
-    """Generalised MP2 start (Eq. inexact_newton_update at t = 0): t1 = 0,
-    t2 = A_F^{-1}(-R2(0)) with R2(0)_ij^ab = (ai|bj)."""
+    """Generalised MP2 start (Eq. inexact_newton_update at t = 0): t = A_F^{-1}(-R(0)), where
+    R1(0)_i^a = f_ia (zero for a Hartree-Fock reference) and R2(0)_ij^ab = (ai|bj)."""
     v = fock.shape[0] - o
     r1, r2, _ = residual(fock, B, o, np.zeros((o, v)), np.zeros((o, o, v, v)))
-    _, t2 = solve_AF(fock, o, np.zeros_like(r1), -r2)
-    return np.zeros((o, v)), t2
+    return solve_AF(fock, o, -r1, -r2)
 
 
 # --------------------------------------------------------------------------
 # the reference solver: fixed point with the diagonal denominator + DIIS
 # --------------------------------------------------------------------------
-def solve_fp_diis(fock, B, o, t1=None, t2=None, tol=1e-10, maxiter=200, shift=0.0, diis_size=8,
-                  diis_start=2, verbose=False, ccd=False):
-    """t <- t - R(t) / (D + shift) with D the diagonal-Fock denominator
-    (Eq. mo_fixed-point_update; App. D for the shift), Pulay DIIS on
-    (t_new, t_new - t).  ccd=True solves CCD (t1 = 0, doubles projections only).
-    Returns (t1, t2, E, history of ||R||)."""
+def fp_diis_iterates(fock, B, o, t1=None, t2=None, shift=0.0, diis_size=8, diis_start=2, ccd=False):
+    """The fixed-point + DIIS iteration one step at a time: t <- t - R(t) / (D + shift) with D
+    the diagonal-Fock denominator (Eq. mo_fixed-point_update; App. D for the shift), Pulay DIIS
+    on (t_new, t_new - t).  Yields (iteration, t1, t2, E, ||R||) at every iterate, before the
+    update is taken; ccd=True solves CCD (t1 = 0, doubles projections only)."""
     v = fock.shape[0] - o
     if t1 is None:
         t1, t2 = mp2_guess(fock, B, o)
@@ -208,19 +206,16 @@ def solve_fp_diis(fock, B, o, t1=None, t2=None, tol=1e-10, maxiter=200, shift=0.
     D1 = fd[None, o:] - fd[:o, None] + shift
     D2 = (fd[None, None, o:, None] + fd[None, None, None, o:] - fd[:o, None, None, None]
           - fd[None, :o, None, None] + shift)
-    vecs, errs, hist = [], [], []
+    vecs, errs = [], []
     if ccd:
         t1 = np.zeros_like(t1)
-    for it in range(maxiter):
+    it = 0
+    while True:
         r1, r2, e = residual(fock, B, o, t1, t2)
         if ccd:
             r1 = np.zeros_like(r1)
         rn = float(np.sqrt(np.sum(r1 * r1) + np.sum(r2 * r2)))
-        hist.append(rn)
-        if verbose:
-            print(f"  fp+diis it {it:3d}  |R| {rn:.3e}  E {e:.12f}")
-        if rn < tol:
-            return t1, t2, e, hist
+        yield it, t1, t2, e, rn
         n1 = t1 - r1 / D1
         n2 = t2 - r2 / D2
         vec = np.concatenate([n1.ravel(), n2.ravel()])
@@ -244,7 +239,31 @@ def solve_fp_diis(fock, B, o, t1=None, t2=None, tol=1e-10, maxiter=200, shift=0.
         t1 = vec[: o * v].reshape(o, v)
         t2 = vec[o * v:].reshape(o, o, v, v)
         t2 = 0.5 * (t2 + t2.transpose(1, 0, 3, 2))
-    r1, r2, e = residual(fock, B, o, t1, t2)
+        it += 1
+
+
+def solve_fp_diis(fock, B, o, t1=None, t2=None, tol=1e-10, maxiter=200, shift=0.0, diis_size=8,
+                  diis_start=2, verbose=False, ccd=False, diverge_at=None, energies=None):
+    """The reference solver: fp_diis_iterates until ||R|| < tol, at most maxiter residual
+    evaluations (then one more at the last update).  diverge_at: stop as soon as ||R||
+    exceeds it (or is not finite); energies: a list that receives E at every iterate.
+    Returns (t1, t2, E, history of ||R||)."""
+    hist = []
+    steps = fp_diis_iterates(fock, B, o, t1, t2, shift=shift, diis_size=diis_size, diis_start=diis_start,
+                             ccd=ccd)
+    for it, t1, t2, e, rn in steps:
+        hist.append(rn)
+        if energies is not None:
+            energies.append(e)
+        if verbose:
+            print(f"  fp+diis it {it:3d}  |R| {rn:.3e}  E {e:.12f}", flush=True)
+        if rn < tol:
+            return t1, t2, e, hist
+        if diverge_at is not None and not (rn <= diverge_at):
+            return t1, t2, e, hist
+        if it + 1 >= maxiter:
+            break
+    _, t1, t2, e, _ = next(steps)
     return t1, t2, e, hist
 
 

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(HERE, "libccpnk.so")
 
 CC_OK, CC_PENDING = 0, 1
 STATUS = {-1: "CC_ERR_INVALID", -2: "CC_ERR_OOM", -3: "CC_ERR_NOT_CONVERGED", -4: "CC_ERR_DIVERGED",
-          -5: "CC_ERR_CUDA", -6: "CC_ERR_TIMEOUT"}
+          -5: "CC_ERR_CUDA", -6: "CC_ERR_TIMEOUT", -7: "CC_ERR_CANCELLED"}
+OPTION = {"stage_cache_bytes": 1, "wait_limit_ns": 2}
 PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3, "df64": 4}
 METHOD = {"fp_diis": 0, "nk": 1, "pnk": 2, "ink": 3}
 
@@ -69,6 +70,9 @@ def lib() -> ctypes.CDLL:
             "cc_last_error": (ctypes.c_char_p, [vp]),
             "cc_ctx_device_bytes": (sz, [vp]),
             "cc_ctx_launches": (u64, [vp]),
+            "cc_ctx_set_option": (i, [vp, i, ctypes.c_longlong]),
+            "cc_ctx_selftest_wait": (i, [vp]),
+            "cc_probe_fma_rate": (i, [i, i, ctypes.POINTER(d)]),
             "cc_ctx_profile": (i, [vp, i]),
             "cc_ctx_profile_get": (i, [vp, ctypes.c_char_p, ctypes.POINTER(u64), ctypes.POINTER(d), ctypes.POINTER(d)]),
             "cc_ctx_profile_list": (i, [vp, ctypes.c_char_p, sz, ctypes.POINTER(sz)]),
@@ -76,6 +80,7 @@ def lib() -> ctypes.CDLL:
             "cc_sys_destroy": (None, [vp]),
             "cc_residual": (i, [vp, vp, vp, vp, vp, vp, ctypes.POINTER(d), i]),
             "cc_jvp": (i, [vp, vp, vp, vp, vp, vp, vp, vp, i]),
+            "cc_jvp_multi": (i, [vp, vp, vp, vp, i, vp, vp, vp, vp, i]),
             "cc_apply_AF": (i, [vp, vp, vp, vp, vp, vp, i, i]),
             "cc_solve": (i, [vp, vp, ctypes.POINTER(SolveOpts), vp, vp, i, ctypes.POINTER(Report)]),
             "cc_energy_noalloc": (i, [vp, vp, vp, vp, vp]),
@@ -83,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "cc_server_destroy": (None, [vp]),
             "cc_serve_submit": (i, [vp, i, i, i, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(u64)]),
             "cc_serve_poll": (i, [vp, u64, ctypes.POINTER(Report), vp, vp]),
+            "cc_serve_cancel": (i, [vp, u64]),
             "cc_serve_times": (i, [vp, u64, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
             "cc_server_stats": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)]),
         }
@@ -166,6 +172,15 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().cc_ctx_launches(self.h))
+
+    def set_option(self, name: str, value: int):
+        """cc_ctx_set_option: 'stage_cache_bytes' (-1 default, 0 off) or 'wait_limit_ns'."""
+        _check(self.h, lib().cc_ctx_set_option(self.h, OPTION[name], int(value)))
+
+    def selftest_wait(self) -> int:
+        """cc_ctx_selftest_wait: the status of one bounded wait that is made to give up
+        (CC_ERR_TIMEOUT, -6, when the bound works)."""
+        return int(lib().cc_ctx_selftest_wait(self.h))
 
     def profile(self, enable: bool = True, all_contractions: bool = False):
         """Turns the kernel timer on (clearing its records) or off. On, it times the ladder
@@ -252,6 +267,16 @@ class System:
                                         _ptr(d2, keep), _ptr(j1, keep), _ptr(j2, keep), _prec(prec)))
         return j1, j2
 
+    def jvp_multi(self, t1, t2, D1, D2, prec="fp64"):
+        """(J1, J2) with J[k] = J(t) D[k] for the k = 0..ndir-1 stacked directions."""
+        keep = []
+        nd = int(D1.shape[0])
+        J1 = _empty_like_kind(t1, (nd, self.o, self.v))
+        J2 = _empty_like_kind(t1, (nd, self.o, self.o, self.v, self.v))
+        _check(self.ctx.h, lib().cc_jvp_multi(self.ctx.h, self.h, _ptr(t1, keep), _ptr(t2, keep), nd, _ptr(D1, keep),
+                                              _ptr(D2, keep), _ptr(J1, keep), _ptr(J2, keep), _prec(prec)))
+        return J1, J2
+
     def apply_AF(self, x1, x2, inverse: int = 0, prec="fp64"):
         """A_F x (inverse=0), A_F^{-1} x by inner GMRES (1) or in the Fock eigenbasis (2)."""
         keep = []
@@ -318,6 +343,10 @@ class Server:
         d["status_code"] = st
         return t1, t2, d
 
+    def cancel(self, ticket: int) -> int:
+        """cc_serve_cancel: drops a waiting request or stops a running one."""
+        return int(lib().cc_serve_cancel(self.h, ticket))
+
     def times(self, ticket: int):
         a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         lib().cc_serve_times(self.h, ticket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
@@ -339,6 +368,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def probe_fma_rate(device: int = 0, fp64: bool = True) -> float:
+    """cc_probe_fma_rate: measured FMA throughput of the FP64 (or FP32) pipe in TFLOP/s."""
+    r = ctypes.c_double()
+    st = lib().cc_probe_fma_rate(device, 1 if fp64 else 0, ctypes.byref(r))
+    if st < 0:
+        raise CCError(st, "cc_probe_fma_rate failed")
+    return r.value
 
 
 def default_opts(method="pnk", prec="fp64", **kw) -> SolveOpts:

@@ -180,6 +180,7 @@ void copy_out(cc_ctx* ctx, double* dst, const double* src, size_t n) {
 
 Engine& engine(cc_sys* sys) {
   if (!sys->eng) sys->eng.reset(new Engine(sys->ctx->ex(), sys->s));
+  else sys->eng->rebind(sys->ctx->ex());  // the context's options may have changed
   return *sys->eng;
 }
 
@@ -266,6 +267,31 @@ size_t cc_ctx_device_bytes(const cc_ctx* ctx) { return ctx && ctx->pool ? ctx->p
 
 uint64_t cc_ctx_launches(const cc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int cc_ctx_set_option(cc_ctx* ctx, int option, long long value) {
+  if (!ctx) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    if (option == CC_OPT_STAGE_CACHE_BYTES) {
+      CC_REQUIRE(value >= -1, CC_ERR_INVALID, "CC_OPT_STAGE_CACHE_BYTES: -1 (default) or a byte count");
+      ctx->stage_cap = value;
+    } else if (option == CC_OPT_WAIT_LIMIT_NS) {
+      CC_REQUIRE(value >= 100000, CC_ERR_INVALID, "CC_OPT_WAIT_LIMIT_NS: at least 1e5 ns");
+      ctx->wait_ns = (unsigned long long)value;
+    } else {
+      fail(CC_ERR_INVALID, "unknown option");
+    }
+    return CC_OK;
+  });
+}
+
+int cc_ctx_selftest_wait(cc_ctx* ctx) {
+  if (!ctx) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    k_wait_selftest(ctx->ex());
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CC_OK;  // the flag the kernel set turns this into CC_ERR_TIMEOUT
+  });
+}
+
 int cc_ctx_profile(cc_ctx* ctx, int enable) {
   if (!ctx) return CC_ERR_INVALID;
   return guarded(ctx, [&]() {
@@ -330,14 +356,19 @@ int cc_sys_create(cc_ctx* ctx, int o, int v, int naux, const double* fock, const
     copy_in(ctx, f.p, fock, (size_t)n * n);
     copy_in(ctx, b.p, B, (size_t)naux * n * n);
     k_asym(ex, naux, n, b.p, chk.p, chk.p + 2);
-    double h[2];
-    CC_CUDA(cudaMemcpyAsync(h, chk.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    k_asym(ex, 1, n, f.p, chk.p + 4, chk.p + 8);
+    double h[6];
+    CC_CUDA(cudaMemcpyAsync(h, chk.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CC_CUDA(cudaStreamSynchronize(ctx->stream));
     CC_REQUIRE(std::isfinite(h[0]) && std::isfinite(h[1]), CC_ERR_INVALID, "B holds non-finite values");
     CC_REQUIRE(h[0] <= 1e-12 * std::max(h[1], 1e-300), CC_ERR_INVALID, "B[P] is not symmetric in its orbital indices");
+    CC_REQUIRE(std::isfinite(h[4]) && std::isfinite(h[5]), CC_ERR_INVALID, "fock holds non-finite values");
     std::unique_ptr<cc_sys> s(new cc_sys);
     s->ctx = ctx;
     system_init(ex, s->s, o, v, naux, f.p, b.p);
+    // the allocation-free energy entry point loads its module and looks up its scratch array
+    // here, so that its own first call on this device has nothing left to load
+    noalloc_prepare(ex, s->s);
     CC_CUDA(cudaStreamSynchronize(ctx->stream));
     *out = s.release();
     return CC_OK;
@@ -394,6 +425,31 @@ int cc_jvp(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2, const d
   });
 }
 
+int cc_jvp_multi(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2, int ndir, const double* d1s,
+                 const double* d2s, double* j1s, double* j2s, cc_precision prec) {
+  if (!ctx || !sys || ndir < 0) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    check_prec(prec);
+    if (ndir == 0) return CC_OK;
+    CC_REQUIRE(d1s && d2s, CC_ERR_INVALID, "NULL direction");
+    const System& s = sys->s;
+    Engine& eng = engine(sys);
+    Exec ex = ctx->ex();
+    const size_t ov = (size_t)s.o * s.v, oovv = s.namp() - ov;
+    DBuf<double> t(ex.pool, s.namp()), d(ex.pool, s.namp()), r(ex.pool, s.namp());
+    load_amplitudes(ctx, s, t1, t2, t.p);
+    eng.value(t.p, r.p, nullptr, CC_FP64);
+    for (int k = 0; k < ndir; ++k) {
+      load_amplitudes(ctx, s, d1s + k * ov, d2s + k * oovv, d.p);
+      eng.tangent(d.p, r.p, prec);
+      if (j1s) copy_out(ctx, j1s + k * ov, r.p, ov);
+      if (j2s) copy_out(ctx, j2s + k * oovv, r.p + ov, oovv);
+    }
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CC_OK;
+  });
+}
+
 int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2, double* y1, double* y2, int inverse,
                 cc_precision prec) {
   if (!ctx || !sys) return CC_ERR_INVALID;
@@ -417,6 +473,15 @@ int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2, do
 
 int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2, int use_guess,
              cc_report* report) {
+  return ccpnk::solve_cancellable(ctx, sys, opts, t1, t2, use_guess, report, nullptr);
+}
+
+}  // extern "C"
+
+namespace ccpnk {
+
+int solve_cancellable(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2, int use_guess,
+                      cc_report* report, const std::atomic<int>* cancel) {
   if (!ctx || !sys || !opts) return CC_ERR_INVALID;
   return guarded(ctx, [&]() {
     check_prec(opts->prec);
@@ -426,7 +491,7 @@ int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, do
     Exec ex = ctx->ex();
     DBuf<double> t(ex.pool, s.namp());
     if (use_guess) load_amplitudes(ctx, s, t1, t2, t.p);
-    int st = solve(ex, s, eng, *opts, t.p, report, use_guess != 0);
+    int st = solve(ex, s, eng, *opts, t.p, report, use_guess != 0, cancel);
     const size_t ov = (size_t)s.o * s.v;
     copy_out(ctx, t1, t.p, ov);
     copy_out(ctx, t2, t.p + ov, s.namp() - ov);
@@ -435,4 +500,5 @@ int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, do
   });
 }
 
-}  // extern "C"
+}  // namespace ccpnk
+

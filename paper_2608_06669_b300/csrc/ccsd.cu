@@ -91,12 +91,20 @@ Engine::Engine(const Exec& ex, const System& s) : ex_(ex), s_(s) {
   alloc(X_, oovv);
   alloc(Y2_, oovv);
   ladder_block_ = ladder_block_for(v);
-  stage_.cap = stage_cache_cap(o, v, P);
-  if (ex.pool->budget()) stage_.cap = std::min(stage_.cap, ex.pool->budget() / 8);
+  rebind(ex);
   W_.alloc(ex.pool, (size_t)ladder_block_ * v * v * v);
   // the tangent's stacked factors [dBt_vv ; Bt_vv] and [Bt_vv ; dBt_vv]
   XsYs_.alloc(ex.pool, 4 * (size_t)P * v * v);
   scratch_.alloc(ex.pool, 64 * 1024);
+}
+
+void Engine::rebind(const Exec& ex) {
+  ex_ = ex;
+  size_t cap = stage_cache_cap(s_.o, s_.v, s_.P);
+  if (ex.pool->budget()) cap = std::min(cap, ex.pool->budget() / 8);
+  if (ex.stage_cap >= 0) cap = (size_t)ex.stage_cap;
+  if (cap < stage_.bytes) stage_.clear();
+  stage_.cap = cap;
 }
 
 void Engine::alloc(Pair& x, size_t n) {

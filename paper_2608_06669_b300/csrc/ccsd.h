@@ -42,6 +42,9 @@ class Engine {
   // J(t) d at the t of the last value() call.
   void tangent(const double* d, double* jd, cc_precision prec);
   const Exec& exec() const { return ex_; }
+  // Takes the context's current settings (wait limit, staged-operand cache size); a smaller
+  // cache drops what it kept.
+  void rebind(const Exec& ex);
   double* scratch() { return scratch_.p; }
   size_t scratch_count() const { return scratch_.n; }
 
@@ -66,6 +69,10 @@ class Engine {
   StageCache stage_;      // staged value-side operands of the tangent program (cleared by value())
   DBuf<double> scratch_;  // reduction partials
 };
+
+// Readies cc_energy_noalloc on the current device for this problem: loads its module, looks up
+// its scratch array and runs its kernels once (so its own calls have nothing left to load).
+void noalloc_prepare(const Exec& ex, const System& s);
 
 // y = A_F x on [x1 | x2] vectors (Eq. Preconditioner, App. C)
 void apply_AF(const Exec& ex, const System& s, const double* x, double* y, cc_precision prec);

@@ -115,6 +115,8 @@ struct Exec {
   int* dev_flag = nullptr;       // device error flag (bounded waits, bad shapes)
   int sm_count = 148;
   Prof* prof = nullptr;
+  unsigned long long wait_ns = 4000000000ull;  // bound on every device-side wait (global timer)
+  long long stage_cap = -1;                    // bytes of kept staged operands (-1: the default)
   void count(uint64_t k = 1) const {
     if (launches) *launches += k;
   }
@@ -227,6 +229,9 @@ struct GemmArgs {
 
 // Tensor-core GEMM (gemm_tc.cu): same contract as the FP64 kernel, run on tcgen05.
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag = nullptr);
+// One kernel whose bounded wait on an mbarrier that nothing arrives at gives up after
+// ex.wait_ns and sets the device error flag (the self-test of the bounded waits).
+void k_wait_selftest(const Exec& ex);
 
 // ---------------------------------------------------------------------------
 // tensors and contractions

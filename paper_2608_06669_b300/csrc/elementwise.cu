@@ -331,6 +331,7 @@ __global__ void asym_partial_kernel(int P, int n, const double* __restrict__ B, 
     double y = B[(Pi * n + q) * n + p];
     mx = fmax(mx, fabs(x - y));
     mb = fmax(mb, fabs(x));
+    if (!isfinite(x)) mb = INFINITY;  // fmax drops NaN operands: report a NaN as an infinite entry
   }
   __shared__ double s1[TPB], s2[TPB];
   s1[threadIdx.x] = mx;
@@ -516,6 +517,7 @@ void k_copy3d(const Exec& ex, int batch, int rows, int cols, const double* src, 
   copy3d_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(batch, rows, cols, src, sbs, sld, dst, dbs, dld);
   LAUNCH_CHECK();
 }
+// out[0] = max |B[P][p][q] - B[P][q][p]|, out[1] = max |B| (infinite if any entry is not finite)
 void k_asym(const Exec& ex, int P, int n, const double* B, double* out, double* scratch) {
   size_t tot = (size_t)P * n * n;
   int nb = grid_for(ex, tot, 2);

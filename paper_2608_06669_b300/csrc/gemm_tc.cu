@@ -46,7 +46,6 @@ constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA producer, MMA issuer, epilo
 constexpr uint32_t A_BYTES = TM * 128;
 constexpr uint32_t B_BYTES = TN * 128;
 constexpr uint32_t TMEM_COLS = 2 * TN;  // two FP32 accumulators of TN columns (all 512)
-constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s bound on any wait
 
 __device__ __forceinline__ long long cidx(const CIdx& c, int x) {
   if (c.e1 == 1 && c.e2 == 1) return (long long)x * c.s0;
@@ -193,6 +192,7 @@ struct TcArgs {
   double* C;
   float* part;  // split-k partial sums [splits][batch][M][N] (splits > 1)
   int* err;
+  unsigned long long wait_ns;  // bound on every mbarrier wait (global timer)
   void* Cs;     // non-null: C in staging layout (offsets from cm/cn/cb count elements)
   long long cs_kpad;
   int cs_nseg, cs_seglo;
@@ -220,8 +220,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// waits for the phase of the given parity to complete; false after WAIT_NS
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// waits for the phase of the given parity to complete; false after limit_ns of global time
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
   unsigned long long t0 = 0;
   for (uint32_t it = 0;; ++it) {
     uint32_t ok;
@@ -235,7 +235,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if ((it & 63) == 0) {
       unsigned long long t = gtime();
       if (t0 == 0) t0 = t;
-      else if (t - t0 > WAIT_NS) return false;
+      else if (t - t0 > limit_ns) return false;
     }
   }
 }
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kb = kb0; kb < kb1; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
-          if (!mbar_wait(empty0 + 8 * s, ph ^ 1)) { ok = false; break; }
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1, g.wait_ns)) { ok = false; break; }
           mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
           tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, kb * TK, m0, bz);
           tma_load_3d(smem_u32(sB + s * B_BYTES), &tmB, full0 + 8 * s, kb * TK, n0, bz);
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       // never leave with copies in flight: the last loads issued must have landed (bounded)
       for (uint32_t r = q > (uint32_t)STAGES ? q - STAGES : 0; r < q; ++r)
-        if (!mbar_wait(full0 + 8 * (r % STAGES), (r / STAGES) & 1)) ok = false;
+        if (!mbar_wait(full0 + 8 * (r % STAGES), (r / STAGES) & 1, g.wait_ns)) ok = false;
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x, ++it) {
         const int acc = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
-        if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1)) { ok = false; break; }
+        if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, g.wait_ns)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * TN);
         int sp, bz, m0, n0, kb0, kb1;
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kb = kb0; kb < kb1; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
-          if (!mbar_wait(full0 + 8 * s, ph)) { ok = false; break; }
+          if (!mbar_wait(full0 + 8 * s, ph, g.wait_ns)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = blockIdx.x; t < g.tiles; t += gridDim.x, ++it) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      bool got = mbar_wait(tfull0 + 8 * acc, use & 1);
+      bool got = mbar_wait(tfull0 + 8 * acc, use & 1, g.wait_ns);
       got = __all_sync(0xffffffffu, got);
       if (!got) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -494,6 +494,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that expects one arrival
+// which never comes, with the same bounded wait as the GEMM's pipeline. After limit_ns it
+// gives up, records the failure in the error flag and the kernel returns normally.
+__global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(b, 0, limit_ns)) atomicExch(err, 1);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   // looked up once per process (thread-safe static initialisation; retried if it threw)
   static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
@@ -552,10 +564,12 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
       for (auto& e : g.cache->ents)
         if (e.key == key) return reinterpret_cast<T*>(e.buf.p);
       if (g.cache->bytes + dbl * 8 <= g.cache->cap) {
+        // allocate first: if the pool throws, no entry is left keyed to a missing buffer
+        DBuf<double> buf(ex.pool, dbl);
         g.cache->ents.emplace_back();
         StageCache::Ent& e = g.cache->ents.back();
         e.key = key;
-        e.buf.alloc(ex.pool, dbl);
+        e.buf = std::move(buf);
         g.cache->bytes += dbl * 8;
         dst = e.buf.p;
       }
@@ -635,6 +649,7 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   a.beta = g.beta;
   a.C = g.C;
   a.err = ex.dev_flag;
+  a.wait_ns = ex.wait_ns;
   a.Cs = g.so ? g.so->base : nullptr;
   a.cs_kpad = g.so ? g.so->kpad : 0;
   a.cs_nseg = g.so ? g.so->nseg : 0;
@@ -691,6 +706,13 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
 }
 
 }  // namespace
+
+void k_wait_selftest(const Exec& ex) {
+  CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "the wait self-test needs a device error flag");
+  wait_selftest_kernel<<<1, 32, 0, ex.stream>>>(ex.dev_flag, ex.wait_ns);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+}
 
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
   CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3, CC_ERR_INVALID,

@@ -16,6 +16,8 @@ struct cc_ctx {
   int* dflag = nullptr;  // device error flag written by bounded waits
   std::string err;
   ccpnk::Prof prof;
+  unsigned long long wait_ns = 4000000000ull;  // CC_OPT_WAIT_LIMIT_NS
+  long long stage_cap = -1;                    // CC_OPT_STAGE_CACHE_BYTES (-1: the default)
   ccpnk::Exec ex() {
     ccpnk::Exec e;
     e.stream = stream;
@@ -24,6 +26,8 @@ struct cc_ctx {
     e.sm_count = sm_count;
     e.dev_flag = dflag;
     e.prof = &prof;
+    e.wait_ns = wait_ns;
+    e.stage_cap = stage_cap;
     return e;
   }
 };
@@ -33,3 +37,9 @@ struct cc_sys {
   ccpnk::System s;
   std::unique_ptr<ccpnk::Engine> eng;
 };
+
+namespace ccpnk {
+// cc_solve with a cancellation flag that another thread may set (the server's cancel).
+int solve_cancellable(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2, int use_guess,
+                      cc_report* report, const std::atomic<int>* cancel);
+}  // namespace ccpnk

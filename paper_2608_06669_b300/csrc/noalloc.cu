@@ -42,6 +42,22 @@ cudaError_t partials_on_current_device(double** out) {
 
 }  // namespace
 
+namespace ccpnk {
+
+// With lazy module loading (the CUDA default) the first use of this file's array or of the
+// energy kernels loads their modules, and loading allocates device memory inside the driver.
+// cc_sys_create calls this, so that path is taken there and not in cc_energy_noalloc.
+void noalloc_prepare(const Exec& ex, const System& s) {
+  double* partials = nullptr;
+  CC_CUDA(partials_on_current_device(&partials));
+  // the kernels run once on scratch of the pool, so this never touches the shared array
+  DBuf<double> t(ex.pool, s.namp()), e(ex.pool, 1), scratch(ex.pool, (size_t)k_energy_partials(ex, s.o, s.v));
+  k_fill(ex, s.namp(), 0.0, t.p);
+  k_energy(ex, s.o, s.v, s.Govov.p, t.p, t.p + (size_t)s.o * s.v, s.f.p + s.o, s.n, e.p, scratch.p);
+}
+
+}  // namespace ccpnk
+
 extern "C" int cc_energy_noalloc(const cc_sys* sys, const double* t1, const double* t2, double* energy,
                                  void* stream) {
   if (!sys || !t1 || !t2 || !energy) return CC_ERR_INVALID;

@@ -9,6 +9,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -34,6 +35,7 @@ struct Request {
   std::vector<double> t1, t2;
   double t_submit = 0, t_admit = 0, t_finish = 0;
   std::string err;
+  std::atomic<int> cancel{0};  // set by cc_serve_cancel; a running solve stops at its next iteration
 };
 
 // Device bytes a solve is expected to hold: the resident problem, the engine's intermediates
@@ -109,10 +111,11 @@ void worker_main(cc_server* srv, int slot) {
       cc_sys* sys = nullptr;
       status = cc_sys_create(ctx, r->o, r->v, r->naux, r->fock.data(), r->B.data(), &sys);
       if (status == CC_OK) {
-        status = cc_solve(ctx, sys, &r->opts, t1.data(), t2.data(), 0, &rep);
+        status = ccpnk::solve_cancellable(ctx, sys, &r->opts, t1.data(), t2.data(), 0, &rep, &r->cancel);
         cc_sys_destroy(sys);
       }
-      if (status < 0 && status != CC_ERR_NOT_CONVERGED && status != CC_ERR_DIVERGED) err = cc_last_error(ctx);
+      if (status < 0 && status != CC_ERR_NOT_CONVERGED && status != CC_ERR_DIVERGED && status != CC_ERR_CANCELLED)
+        err = cc_last_error(ctx);
     } else {
       err = "no device context for this slot";
     }
@@ -212,6 +215,36 @@ int cc_serve_poll(cc_server* srv, uint64_t ticket, cc_report* report, double* t1
   r->t2.clear();
   r->t2.shrink_to_fit();
   return r->status;
+}
+
+int cc_serve_cancel(cc_server* srv, uint64_t ticket) {
+  if (!srv) return CC_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->all.find(ticket);
+    if (it == srv->all.end() || it->second->released) return CC_ERR_INVALID;
+    Request* r = it->second.get();
+    if (r->done) return CC_OK;  // finished already: its own status stands
+    auto q = std::find(srv->queue.begin(), srv->queue.end(), r);
+    if (q != srv->queue.end()) {  // still waiting: drop it without running
+      srv->queue.erase(q);
+      r->status = CC_ERR_CANCELLED;
+      r->report = cc_report{};
+      r->report.status = CC_ERR_CANCELLED;
+      r->t1.assign((size_t)r->o * r->v, 0.0);
+      r->t2.assign((size_t)r->o * r->o * r->v * r->v, 0.0);
+      r->t_admit = r->t_finish = srv->now();
+      r->done = true;
+      r->fock.clear();
+      r->fock.shrink_to_fit();
+      r->B.clear();
+      r->B.shrink_to_fit();
+    } else {
+      r->cancel.store(1);  // running: the solve stops between outer iterations
+    }
+  }
+  srv->cv.notify_all();
+  return CC_OK;
 }
 
 int cc_serve_times(cc_server* srv, uint64_t ticket, double* t_submit, double* t_admit, double* t_finish) {

@@ -255,7 +255,7 @@ void solve_AF(const Exec& ex, System& s, const double* b, double* x, cc_precisio
 // nonlinear solvers
 // ---------------------------------------------------------------------------
 int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, double* t, cc_report* rep,
-          bool use_guess) {
+          bool use_guess, const std::atomic<int>* cancel) {
   auto t_start = std::chrono::steady_clock::now();
   const size_t n = s.namp();
   const int o = s.o, v = s.v;
@@ -285,6 +285,8 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     return opt.max_seconds > 0 &&
            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > opt.max_seconds;
   };
+  // a cancelled solve stops between outer iterations, like one out of time
+  auto cancelled = [&]() { return cancel && cancel->load() != 0; };
   auto residual = [&](const double* tt, double* rr, double* e_host) -> double {
     eng.value(tt, rr, dev.p + 1, outer);
     if (opt.ccd) k_fill(ex, n1, 0.0, rr);
@@ -296,12 +298,17 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     return std::sqrt(std::max(hv[0], 0.0));
   };
 
-  // generalised MP2 start (Eq. inexact_newton_update at t = 0): t1 = 0, t2 = A_F^{-1}(-R2(0)).
-  // At t = 0 every amplitude term of the residual vanishes and R2(0)_ij^ab = (ia|jb), so the
-  // start needs no residual evaluation.
+  // generalised MP2 start (Eq. inexact_newton_update at t = 0): t = A_F^{-1}(-R(0)). At t = 0
+  // every amplitude term of the residual vanishes: R1(0)_i^a = f_ia and R2(0)_ij^ab = (ia|jb),
+  // so the start needs no residual evaluation (t1 stays 0 in CCD mode and whenever f_ov = 0).
   if (!use_guess) {
     k_fill(ex, n, 0.0, t);
-    k_fill(ex, n1, 0.0, r.p);
+    if (opt.ccd) {
+      k_fill(ex, n1, 0.0, r.p);
+    } else {
+      k_copy2d(ex, o, v, s.f.p + o, s.n, r.p, v);
+      k_scale(ex, n1, -1.0, r.p);
+    }
     k_ovov_to_oovv(ex, o, v, s.Govov.p, r.p + n1, -1.0);
     AFinv(r.p, t);
   } else if (opt.ccd) {
@@ -328,6 +335,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
       if (!std::isfinite(rn) || rn > 1e8) { status = CC_ERR_DIVERGED; break; }
       if (rn < opt.tol) { status = CC_OK; break; }
       if (out_of_time()) break;
+      if (cancelled()) { status = CC_ERR_CANCELLED; break; }
       st.newton_iters++;
       // e = -R / (D + shift), t_new = t + e
       k_denom_divide(ex, o, v, fdiag.p, opt.level_shift, r.p, r.p + (size_t)o * v, tmp.p, tmp.p + (size_t)o * v, -1.0);
@@ -412,6 +420,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
       if (!std::isfinite(rn) || rn > 1e8) { status = CC_ERR_DIVERGED; break; }
       if (rn < opt.tol) { status = CC_OK; break; }
       if (out_of_time()) break;
+      if (cancelled()) { status = CC_ERR_CANCELLED; break; }
       st.newton_iters++;
       if (opt.method == CC_INK) {
         // t <- t + A_F^{-1}(-r)

@@ -1,6 +1,7 @@
 // Linear and nonlinear solvers of the Newton-Krylov family (host control, device vectors).
 #pragma once
 
+#include <atomic>
 #include <functional>
 
 #include "ccsd.h"
@@ -27,8 +28,9 @@ void solve_AF(const Exec& ex, System& s, const double* b, double* x, cc_precisio
               int m_max, bool direct, SolveStats* st);
 
 // The nonlinear solve behind cc_solve; t holds [t1 | t2] (guess in, solution out).
+// cancel (may be null): a flag another thread sets to stop the solve between outer iterations.
 int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& o, double* t, cc_report* rep,
-          bool use_guess);
+          bool use_guess, const std::atomic<int>* cancel = nullptr);
 
 // Host helpers
 double host_dot(const Exec& ex, size_t n, const double* x, const double* y, double* dev_tmp, double* scratch);

@@ -133,3 +133,73 @@ def test_mixed_pnk_workload(ctx):
     _, _, rep = gsys(ctx, s).solve("pnk", "tf32")
     assert rep["status_code"] == 0, rep
     assert abs(rep["energy"] - ref) < 1e-8
+
+
+def test_jvp_directions_share_the_kept_staging(ctx):
+    """Several JVPs at one point (cc_jvp_multi) keep the tensor-core staging of the fixed,
+    value-side operands between directions; each result equals a JVP computed on its own
+    (where every staged operand is gathered afresh) bit for bit, and the oracle's JVP within
+    the three-pass bound. With the cache turned off the results are the same bits again."""
+    o, v, naux = 4, 40, 24
+    s = synth.make_system(o, v, naux, seed=33, gauge="haar")
+    rng = np.random.default_rng(6)
+    t1, t2 = synth.random_amplitudes(rng, o, v, 0.05, 0.05)
+    dirs = [synth.random_amplitudes(rng, o, v, 0.05, 0.05) for _ in range(3)]
+    D1 = np.stack([d[0] for d in dirs])
+    D2 = np.stack([d[1] for d in dirs])
+    g = gsys(ctx, s)
+    J1, J2 = g.jvp_multi(t1, t2, D1, D2, prec="tf32x3")
+    for k, (d1, d2) in enumerate(dirs):
+        j1, j2 = g.jvp(t1, t2, d1, d2, prec="tf32x3")
+        assert np.array_equal(j1, J1[k]) and np.array_equal(j2, J2[k]), k
+        p1, p2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+        scale = max(np.abs(p1).max(), np.abs(p2).max())
+        assert max(np.abs(J1[k] - p1).max(), np.abs(J2[k] - p2).max()) < 1e-6 * scale
+    ctx.set_option("stage_cache_bytes", 0)
+    try:
+        K1, K2 = g.jvp_multi(t1, t2, D1, D2, prec="tf32x3")
+    finally:
+        ctx.set_option("stage_cache_bytes", -1)
+    assert np.array_equal(K1, J1) and np.array_equal(K2, J2)
+
+
+def test_mixed_solve_is_the_same_with_and_without_kept_staging(ctx):
+    s = synth.workload("o10v90_rotated")
+    g = gsys(ctx, s)
+    a1, a2, with_cache = g.solve("pnk", "tf32x3", af_direct=1)
+    ctx.set_option("stage_cache_bytes", 0)
+    try:
+        b1, b2, without = g.solve("pnk", "tf32x3", af_direct=1)
+    finally:
+        ctx.set_option("stage_cache_bytes", -1)
+    assert with_cache["status_code"] == 0 == without["status_code"]
+    for k in ("newton_iters", "jvps", "krylov_iters", "residual_evals"):
+        assert with_cache[k] == without[k], k
+    assert with_cache["energy"] == without["energy"] and np.array_equal(a2, b2)
+
+
+def test_mixed_jvp_error_table(ctx):
+    """The error of each tensor-core precision's JVP against the FP64 oracle on the o=10, v=90
+    workload at its MP2 start (normwise: max element error over max element). The table is
+    written to $CCPNK_REPORT_DIR/jvp_error_table.json when that variable is set."""
+    import os
+
+    s = synth.workload("o10v90_rotated")
+    o, v = s.o, s.v
+    t1, t2 = cc.mp2_guess(s.fock, s.B, o)
+    d1, d2 = synth.random_amplitudes(np.random.default_rng(4), o, v, 0.01, 0.01)
+    p1, p2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+    scale = max(np.abs(p1).max(), np.abs(p2).max())
+    g = gsys(ctx, s)
+    table = {}
+    for prec, bound in (("tf32", 5e-3), ("bf16x3", 2e-5), ("tf32x3", 1e-6), ("df64", 1e-10), ("fp64", 1e-10)):
+        j1, j2 = g.jvp(t1, t2, d1, d2, prec=prec)
+        err = max(np.abs(j1 - p1).max(), np.abs(j2 - p2).max()) / scale
+        table[prec] = err
+        assert err < bound, (prec, err)
+    assert table["tf32x3"] < table["bf16x3"] < table["tf32"]
+    out = os.environ.get("CCPNK_REPORT_DIR")
+    if out:
+        with open(os.path.join(out, "jvp_error_table.json"), "w") as fh:
+            json.dump({"workload": "o10v90_rotated, MP2 start, random direction (scale 0.01)",
+                       "normwise_error_vs_oracle": table}, fh, indent=1)

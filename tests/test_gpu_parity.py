@@ -276,3 +276,32 @@ def test_kernel_timer_levels(ctx):
     assert set(lvl1) < set(lvl2) and any(k.endswith(".f64") and ">" in k for k in lvl2)
     assert all(n >= 1 and ms >= 0.0 for n, ms, _ in lvl2.values())
     assert np.array_equal(r2, q2) and np.array_equal(r1, q1) and e == eq
+
+
+@pytest.mark.parametrize("name,shift", [("o5v20_canonical", 0.2), ("o10v90_rotated", 0.2)])
+def test_level_shifted_fp_diis_reaches_the_oracle_root(ctx, name, shift):
+    """FP + DIIS with the level shift of App. D (every denominator D + shift) lands on the
+    oracle's root, and its amplitudes zero the oracle residual."""
+    s = synth.workload(name)
+    ref = _golden()[name]["e_corr"]
+    t1, t2, rep = gpu_system(ctx, s).solve("fp_diis", "fp64", level_shift=shift, max_outer=500)
+    assert rep["status_code"] == 0, rep
+    assert abs(rep["energy"] - ref) < 1e-8
+    if name == "o5v20_canonical":
+        q1, q2, eq = cc.residual(s.fock, s.B, s.o, t1, t2)
+        assert np.sqrt((q1 ** 2).sum() + (q2 ** 2).sum()) < 1e-8 and abs(eq - rep["energy"]) < 1e-10
+
+
+def test_mp2_start_with_singles_driving_term(ctx):
+    """A non-Hartree-Fock reference (f_ov != 0): the generalised MP2 start is the inexact
+    Newton step at t = 0 (Eq. inexact_newton_update), t = A_F^{-1}(-R(0)) with R1(0) = f_ov,
+    singles included. max_outer = 0 returns the start itself."""
+    o, v, naux = 3, 9, 8
+    s = synth.make_system(o, v, naux, seed=12, gauge="haar")
+    fov = np.random.default_rng(4).normal(0, 0.05, size=(o, v))
+    s.fock[:o, o:] = fov
+    s.fock[o:, :o] = fov.T
+    t1, t2, rep = gpu_system(ctx, s).solve("pnk", "fp64", af_direct=1, max_outer=0)
+    q1, q2 = cc.mp2_guess(s.fock, s.B, o)
+    assert np.abs(q1).max() > 1e-3
+    assert rel_err(t1, q1) <= TOL64 and rel_err(t2, q2) <= TOL64

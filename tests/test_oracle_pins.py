@@ -122,6 +122,26 @@ def test_mp2_closed_form(gauge):
     assert abs(cc.energy(s.fock, s.B, o, t1, t2) - e_mp2) < 1e-12
 
 
+def test_mp2_start_singles_closed_form():
+    """P3 with a singles driving term: for a reference with f_ov != 0 the generalised MP2
+    start's singles are the first-order amplitudes t_i^a = -f_ia / (eps_a - eps_i) in the
+    canonical gauge (the closed form of A_F^{-1}(-R1(0)) with R1(0) = f_ov)."""
+    o, v, naux = 3, 5, 6
+    s = synth.make_system(o, v, naux, seed=41, gauge="canonical")
+    fov = np.random.default_rng(2).normal(0, 0.05, size=(o, v))
+    f = s.fock.copy()
+    f[:o, o:] = fov
+    f[o:, :o] = fov.T
+    t1, t2 = cc.mp2_guess(f, s.B, o)
+    e = np.diag(f)
+    assert _norm(t1 + fov / (e[None, o:] - e[:o, None])) < 1e-15
+    # the doubles are the closed-form first-order doubles, untouched by f_ov
+    Bov = s.B[:, :o, o:]
+    iajb = np.einsum("Xia,Xjb->iajb", Bov, Bov)
+    D = e[None, None, o:, None] + e[None, None, None, o:] - e[:o, None, None, None] - e[None, :o, None, None]
+    assert _norm(t2 + iajb.transpose(0, 2, 1, 3) / D) < 1e-14
+
+
 def test_gauge_covariance():
     """P4: rotating the problem by U = diag(U_o, U_v) rotates the residual the
     same way, R(U t) = U R(t), and leaves the energy unchanged (the gauge
