@@ -56,9 +56,14 @@ typedef enum {
                            tcgen05 kind::f16, FP32 accumulate (about 16 significant bits) */
   CC_MIXED_TF32X3 = 3,  /* 3-pass TF32 split: x = hi + lo, a b ~ hi hi + hi lo + lo hi on tcgen05,
                            FP32 accumulate (about FP32 accuracy at a third of the TF32 rate) */
-  CC_DF64 = 4           /* double-float: FP64 operands as FP32 pairs on the FP32 pipe (error-free
+  CC_DF64 = 4,          /* double-float: FP64 operands as FP32 pairs on the FP32 pipe (error-free
                            products, two-sum accumulation; about 48 significant bits), for the
                            residual when FP64 FMA throughput is the limit */
+  CC_FP64_EMU = 5       /* FP64-accurate contractions on the tensor cores: each FP64 row split into
+                           8 BF16 slices of 6-bit integer digits under a per-row exponent (Ozaki's
+                           error-free splitting), slice products summed exactly in FP32 chunks on
+                           tcgen05 kind::f16 and combined in 64-bit integer fixed point; 48
+                           significant bits per operand. Thin contractions stay on the FP64 pipe */
 } cc_precision;
 
 typedef enum {
@@ -92,7 +97,7 @@ typedef struct {
                             only the doubles projections are solved */
   double max_seconds;    /* > 0: stop with CC_ERR_NOT_CONVERGED once a solve has run this long
                             (checked between outer iterations) */
-  int outer_prec;        /* precision of the outer residual: CC_FP64 (default) or CC_DF64 */
+  int outer_prec;        /* precision of the outer residual: CC_FP64 (default), CC_DF64 or CC_FP64_EMU */
 } cc_solve_opts;
 
 typedef struct {

@@ -117,10 +117,15 @@ def residual(fock: np.ndarray, B: np.ndarray, o: int, t1: np.ndarray, t2: np.nda
 
     # doubles: A2 (constant + particle-particle ladder)
     R2 = g_vovo.transpose(1, 3, 0, 2).copy()
+    # sum_cd (ac|bd)~ t_ij^cd, one a at a time: with G_a[b, d, c] = (ac|bd)~ = sum_X Bt[X,b,d] Bt[X,a,c]
+    # and t2 read as [ij, (d, c)], the sum over (d, c) is one matrix product (no permuted copies)
     Bvv = _blk(Bt, o, "v", "v")
-    for a in range(Bvv.shape[1]):
-        g_a = np.einsum("Xc,Xbd->cbd", Bvv[:, a, :], Bvv, optimize=True)  # (ac|bd)~ for this a
-        R2[:, :, a, :] += np.einsum("cbd,ijcd->ijb", g_a, t2, optimize=True)
+    nv = Bvv.shape[1]
+    Bflat = Bvv.reshape(Bvv.shape[0], nv * nv)                          # [X, (b, d)]
+    t2_dc = np.ascontiguousarray(t2.transpose(0, 1, 3, 2)).reshape(o * o, nv * nv)  # [ij, (d, c)]
+    for a in range(nv):
+        G_a = (Bflat.T @ Bvv[:, a, :]).reshape(nv, nv * nv)           # [b, (d, c)] = (ac|bd)~
+        R2[:, :, a, :] += (t2_dc @ G_a.T).reshape(o, o, nv)
     # B2 (hole ladder with its quadratic part)
     W = g_oooo + np.einsum("ijcd,kcld->kilj", t2, g_ovov, optimize=True)
     R2 += np.einsum("klab,kilj->ijab", t2, W, optimize=True)

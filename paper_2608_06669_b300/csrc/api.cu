@@ -185,8 +185,9 @@ Engine& engine(cc_sys* sys) {
 }
 
 void check_prec(cc_precision p) {
-  CC_REQUIRE(p == CC_FP64 || p == CC_MIXED_TF32 || p == CC_MIXED_TF32X3 || p == CC_MIXED_BF16X3 || p == CC_DF64, CC_ERR_INVALID,
-             "unknown precision");
+  CC_REQUIRE(p == CC_FP64 || p == CC_MIXED_TF32 || p == CC_MIXED_TF32X3 || p == CC_MIXED_BF16X3 || p == CC_DF64 ||
+                 p == CC_FP64_EMU,
+             CC_ERR_INVALID, "unknown precision");
 }
 
 // [t1 | t2] with t2 symmetrised: T2 only depends on t_ij^ab + t_ji^ba

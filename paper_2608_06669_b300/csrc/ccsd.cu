@@ -136,9 +136,11 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
   double* L = Y2_.val.p;
   const char* tb = prec == CC_FP64 ? "ladder_build.fp64"
                    : prec == CC_DF64 ? "ladder_build.df64"
+                   : prec == CC_FP64_EMU ? "ladder_build.emu"
                    : prec == CC_MIXED_BF16X3 ? "ladder_build.bf16" : "ladder_build.tf32";
   const char* tc = prec == CC_FP64 ? "ladder_contract.fp64"
                    : prec == CC_DF64 ? "ladder_contract.df64"
+                   : prec == CC_FP64_EMU ? "ladder_contract.emu"
                    : prec == CC_MIXED_BF16X3 ? "ladder_contract.bf16" : "ladder_contract.tf32";
   const bool tensor = prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3;
   // tensor cores: the slab goes straight from the first GEMM's epilogue, as TF32 or BF16

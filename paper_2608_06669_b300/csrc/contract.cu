@@ -418,10 +418,17 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
     // kernel is estimated to be faster it runs there (more accurate, never less).
     const double flops = 2.0 * g.M * (double)g.N * g.K * g.batch;
     const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
-    const int tk = prec == CC_MIXED_BF16X3 ? 64 : 32;
+    const int tk = prec == CC_MIXED_BF16X3 || prec == CC_FP64_EMU ? 64 : 32;
     const double padded = 2.0 * ((g.M + 127) / 128 * 128.0) * ((g.N + 255) / 256 * 256.0) *
                           ((g.K + tk - 1) / tk * (double)tk) * nseg * g.batch;
-    const double t_tc = 12e-6 + padded / 4.5e14 + 8.0 * g.M * (double)g.N * g.batch / 1e12;
+    double t_tc = 12e-6 + padded / 4.5e14 + 8.0 * g.M * (double)g.N * g.batch / 1e12;
+    if (prec == CC_FP64_EMU) {
+      // 36 slice products on kind::f16, the exact partial sums (one per chunk of up to 1024 k,
+      // written and read once in FP32), the digit staging of both operands
+      const double kp = (g.K + 63) / 64 * 64.0, chunks = 36.0 * kp / 1024.0 + 8.0;
+      t_tc = 20e-6 + 36.0 * padded / 1.2e15 + chunks * 8.0 * g.M * (double)g.N * g.batch / 5e12 +
+             ((double)g.M + g.N) * kp * g.batch * 24.0 / 5e12;
+    }
     // the FP64 kernel's parallelism: 16 x 16 tiles, k split at most 64 ways
     const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch *
                           std::min(64, std::max(1, g.K / 32));
@@ -434,6 +441,7 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
       return;
     }
     prec = CC_FP64;
+    (void)flops;
   }
   // (a few outputs over a long k stay on the split-k GEMM path, which spreads k over SMs)
   if (prec == CC_FP64 && (g.N == 1 || g.M == 1) && g.K > 0 &&

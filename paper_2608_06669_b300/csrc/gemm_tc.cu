@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 
 #include "common.h"
 
@@ -182,10 +183,130 @@ __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64-accurate products on the tensor cores: Ozaki's error-free splitting (Ozaki, Ogita,
+// Oishi and Rump, Numer. Algorithms 59 (2012) 95; on tensor cores: Mukunoki, Ozaki, Ogita and
+// Imamura, ICCS 2020). Every row x of an operand (a row of A, a column of B) is written as
+//   x_k = sign(x_k) sum_{s=1..S} d_s(x_k) 2^(sigma - OZ_BETA s) + (error < 2^(sigma - OZ_BETA S)),
+// with sigma the row's exponent (|x_k| < 2^sigma) and integer digits 0 <= d_s < 2^OZ_BETA, which
+// BF16 holds exactly. A product of two digit slices is then a sum of integers: each MMA chunk of
+// at most OZ_NK k blocks sums at most OZ_NK * 64 products below 2^(2 OZ_BETA), under 2^22, which
+// the FP32 accumulator represents exactly. The slice products of one level L = s + t share the
+// scale 2^(sigma_i + tau_j - OZ_BETA L); levels up to S + 1 are kept (the first term dropped is
+// below 2^(-OZ_BETA S) of the leading one) and added in 64-bit integer fixed point, so the only
+// rounding is the final conversion to FP64.
+// ---------------------------------------------------------------------------
+constexpr int OZ_S = 8;      // slices per operand: 48 significant bits
+constexpr int OZ_BETA = 6;   // bits per slice digit
+constexpr int OZ_NK = 16;    // k blocks (of 64) per exact FP32 chunk: 16 * 64 * 63^2 < 2^22
+
+// One warp per staged row: pass 1 finds the largest exponent of the row, pass 2 writes the
+// S digit slices of every element as BF16 into the K-major staging layout
+// out[b][r][seg * k_pad + k] (segment s - 1 holds slice s for A; B holds slice t in segment
+// S - t), zeros outside rows x K. expo[b * rows_pad + r] = sigma. The digits come from the
+// FP64 bit pattern with integer shifts (no FP64 arithmetic).
+__global__ void oz_stage_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
+                                int batch, int rows_pad, int k_pad, int rev, __nv_bfloat16* __restrict__ out,
+                                int* __restrict__ expo) {
+  const int lane = threadIdx.x & 31;
+  const long long items = (long long)batch * rows_pad;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const size_t row_len = (size_t)OZ_S * k_pad;
+  for (long long q = w0; q < items; q += nw) {
+    const int b = (int)(q / rows_pad), r = (int)(q - (long long)b * rows_pad);
+    __nv_bfloat16* row = out + (size_t)q * row_len;
+    if (r >= rows) {
+      for (size_t k = lane; k < row_len; k += 32) row[k] = __float2bfloat16_rn(0.0f);
+      if (lane == 0) expo[q] = 0;
+      continue;
+    }
+    const double* srow = src + cidx(bix, b) + cidx(rix, r);
+    unsigned emax = 1;  // biased exponent; 1 also covers zeros and subnormals
+    CWalk kw;
+    kw.init(kix, lane);
+    for (int k = lane; k < K; k += 32) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
+      emax = max(emax, (unsigned)((bits >> 52) & 0x7FF));
+      kw.step(kix, 32);
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (lane == 0) expo[q] = (int)emax - 1022;  // every |x| of the row is below 2^(emax - 1022)
+    kw.init(kix, lane);
+    for (int k = lane; k < k_pad; k += 32) {
+      unsigned long long qv = 0, neg = 0;
+      if (k < K) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
+        unsigned e = (unsigned)((bits >> 52) & 0x7FF);
+        unsigned long long m = bits & ((1ull << 52) - 1);
+        if (e) m |= 1ull << 52;
+        else e = 1;
+        neg = bits >> 63;
+        // |x| = m 2^(e - 1075); in units of 2^(sigma - beta S): m >> (emax - e + 53 - beta S)
+        const unsigned sh = emax - e + 53 - OZ_BETA * OZ_S;
+        qv = sh >= 64 ? 0ull : (m >> sh);
+        kw.step(kix, 32);
+      }
+#pragma unroll
+      for (int sl = 1; sl <= OZ_S; ++sl) {
+        const int d = (int)((qv >> (OZ_BETA * (OZ_S - sl))) & ((1u << OZ_BETA) - 1));
+        const float f = neg ? -(float)d : (float)d;
+        const int seg = rev ? OZ_S - sl : sl - 1;
+        row[(size_t)seg * k_pad + k] = __float2bfloat16_rn(f);
+      }
+    }
+  }
+}
+
+// C = alpha * sum over levels of the exact chunk sums (scaled per level) + beta * C. One warp
+// per piece of an output row; the chunk sums are integers below 2^22, added per level in int64
+// and combined in 64-bit fixed point with the levels' scales 2^(OZ_BETA (S + 1 - L) - gsh)
+// (gsh > 0 drops low bits of the smallest levels so that the sum stays below 2^62).
+__global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, int nsplit, int kseg, int gsh,
+                                  const int* __restrict__ expA, int rowsA_pad, const int* __restrict__ expB,
+                                  int rowsB_pad, int piece) {
+  const int lane = threadIdx.x & 31;
+  const size_t tot = (size_t)g.batch * g.M * g.N;
+  const int pieces = (g.N + piece - 1) / piece;
+  const long long items = (long long)g.batch * g.M * pieces;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = w0; it < items; it += nw) {
+    const long long qrow = it / pieces;
+    const int n0 = (int)(it - qrow * pieces) * piece, n1 = min(g.N, n0 + piece);
+    const int b = (int)(qrow / g.M), m = (int)(qrow - (long long)b * g.M);
+    const long long rowoff = cidx(g.cb, b) + cidx(g.cm, m);
+    const float* pr = part + (size_t)qrow * g.N;
+    const int ea = expA[(size_t)b * rowsA_pad + m];
+    CWalk cw;
+    cw.init(g.cn, n0 + lane);
+    for (int n = n0 + lane; n < n1; n += 32) {
+      long long acc = 0;
+      int v = 0;
+      for (int L = 2; L <= OZ_S + 1; ++L) {
+        const int nch = ((L - 1) * kseg + OZ_NK - 1) / OZ_NK;
+        long long lv = 0;
+        for (int c = 0; c < nch; ++c, ++v) lv += (long long)__float2int_rn(pr[(size_t)v * tot + n]);
+        const int sh = OZ_BETA * (OZ_S + 1 - L) - gsh;
+        acc += sh >= 0 ? (lv << sh) : ((lv + (1ll << (-sh - 1))) >> (-sh));
+      }
+      (void)nsplit;
+      const int e = ea + expB[(size_t)b * rowsB_pad + n] - OZ_BETA * (OZ_S + 1) + gsh;
+      const double val = g.alpha * ldexp((double)acc, e);
+      double* c = g.C + rowoff + cw.off;
+      *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
+      cw.step(g.cn, 32);
+    }
+  }
+}
+
 struct TcArgs {
   int M, N, kblocks, num_m, num_n, tiles;  // tiles counts splits x batch x num_m x num_n
   int m_fast;                             // 1: consecutive tiles walk down m (they share a B tile)
   int splits, kchunk;                     // split-k: k blocks [s * kchunk, (s + 1) * kchunk)
+  // Ozaki slices (oz_S > 0): the operands hold oz_S slices of oz_kseg k blocks each, and the
+  // splits enumerate the (level, chunk) pairs of the slice products (see oz_split_range)
+  int oz_S, oz_kseg, oz_nk;
   int batch;
   CIdx cm, cn, cb;
   double alpha, beta;
@@ -265,9 +386,30 @@ constexpr uint32_t idesc() {
          ((uint32_t)(TM >> 4) << 24);
 }
 
-// tile t -> (split, batch entry, first row, first column, k-block range)
-__device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int& bz, int& m0, int& n0, int& kb0,
-                                            int& kb1) {
+// Split sp of an Ozaki product -> its level L and k-block ranges. Level L = s + t collects the
+// slice products A_s B_t (s, t >= 1): A's slices 1..L-1 are its segments 0..L-2, B holds its
+// slices in reverse order (slice t in segment S - t), so the partners L-1..1 are B's segments
+// S-L+1..S-1 and one level is a single run of (L-1) kseg k blocks in both operands. A level is
+// cut into chunks of at most nk k blocks, each one split (its own FP32 partial sum).
+__host__ __device__ __forceinline__ int oz_split_range(int S, int kseg, int nk, int sp, int& kA0, int& kB0,
+                                                      int& nkb) {
+  for (int L = 2; L <= S + 1; ++L) {
+    const int len = (L - 1) * kseg, nch = (len + nk - 1) / nk;
+    if (sp < nch) {
+      kA0 = sp * nk;
+      kB0 = (S - L + 1) * kseg + sp * nk;
+      nkb = min(nk, len - sp * nk);
+      return L;
+    }
+    sp -= nch;
+  }
+  kA0 = kB0 = nkb = 0;
+  return 0;
+}
+
+// tile t -> (split, batch entry, first row, first column, k blocks of A and of B, their count)
+__device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int& bz, int& m0, int& n0, int& kA0,
+                                            int& kB0, int& nkb) {
   const int per = g.num_m * g.num_n;
   const int outer = t / per;
   sp = outer / g.batch;
@@ -280,8 +422,12 @@ __device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int
     m0 = (r / g.num_n) * TM;
     n0 = (r % g.num_n) * TN;
   }
-  kb0 = sp * g.kchunk;
-  kb1 = min(g.kblocks, kb0 + g.kchunk);
+  if (g.oz_S > 0) {
+    oz_split_range(g.oz_S, g.oz_kseg, g.oz_nk, sp, kA0, kB0, nkb);
+  } else {
+    kA0 = kB0 = sp * g.kchunk;
+    nkb = min(g.kblocks, kA0 + g.kchunk) - kA0;
+  }
 }
 
 // shared memory: STAGES x (A tile, B tile), the epilogue's turn-around tiles, barriers
@@ -344,15 +490,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       uint32_t q = 0;  // pipeline slot counter, continued across tiles
       for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
-        int sp, bz, m0, n0, kb0, kb1;
-        tile_coords(g, t, sp, bz, m0, n0, kb0, kb1);
-        for (int kb = kb0; kb < kb1; ++kb, ++q) {
+        int sp, bz, m0, n0, kA0, kB0, nkb;
+        tile_coords(g, t, sp, bz, m0, n0, kA0, kB0, nkb);
+        for (int kb = 0; kb < nkb; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
           if (!mbar_wait(empty0 + 8 * s, ph ^ 1, g.wait_ns)) { ok = false; break; }
           mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
-          tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, kb * TK, m0, bz);
-          tma_load_3d(smem_u32(sB + s * B_BYTES), &tmB, full0 + 8 * s, kb * TK, n0, bz);
+          tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, (kA0 + kb) * TK, m0, bz);
+          tma_load_3d(smem_u32(sB + s * B_BYTES), &tmB, full0 + 8 * s, (kB0 + kb) * TK, n0, bz);
         }
       }
       // never leave with copies in flight: the last loads issued must have landed (bounded)
@@ -370,9 +516,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, g.wait_ns)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * TN);
-        int sp, bz, m0, n0, kb0, kb1;
-        tile_coords(g, t, sp, bz, m0, n0, kb0, kb1);
-        for (int kb = kb0; kb < kb1; ++kb, ++q) {
+        int sp, bz, m0, n0, kA0, kB0, nkb;
+        tile_coords(g, t, sp, bz, m0, n0, kA0, kB0, nkb);
+        for (int kb = 0; kb < nkb; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
           if (!mbar_wait(full0 + 8 * s, ph, g.wait_ns)) { ok = false; break; }
@@ -381,7 +527,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < TK / UK; ++j) {
             const uint64_t da = sdesc(a0 + j * 32), db = sdesc(b0 + j * 32);  // UK elements = 32 bytes
-            const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
+            const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
             if constexpr (BF) {
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
@@ -418,8 +564,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       got = __all_sync(0xffffffffu, got);
       if (!got) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      int sp, bz, m0, n0, kb0, kb1;
-      tile_coords(g, t, sp, bz, m0, n0, kb0, kb1);
+      int sp, bz, m0, n0, kA0, kB0, nkb;
+      tile_coords(g, t, sp, bz, m0, n0, kA0, kB0, nkb);
       // each lane locates one of the warp's 32 rows once; the store loop broadcasts them
       const int my_row = m0 + quad * 32 + lane;
       long long my_off = -1;
@@ -640,6 +786,7 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   }
   a.kchunk = (a.kblocks + splits - 1) / splits;
   splits = (a.kblocks + a.kchunk - 1) / a.kchunk;  // no empty split
+  a.oz_S = a.oz_kseg = a.oz_nk = 0;
   a.splits = splits;
   a.tiles = (int)(base_tiles * splits);
   a.cm = g.cm;
@@ -705,6 +852,99 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
 }
 
+// FP64-accurate contraction on the tensor cores (see oz_stage_kernel): stage both operands
+// as OZ_S BF16 digit slices with per-row exponents, run every (level, chunk) slice product as a
+// split of one persistent kind::f16 launch writing exact FP32 partial sums, and combine them in
+// integer fixed point into C = alpha A B + beta C.
+int oz_splits(int kseg) {
+  int n = 0;
+  for (int L = 2; L <= OZ_S + 1; ++L) n += ((L - 1) * kseg + OZ_NK - 1) / OZ_NK;
+  return n;
+}
+
+void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
+  constexpr int TK = Elt<true>::TK;
+  const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
+  const int k_pad = (g.K + TK - 1) / TK * TK;
+  const int kseg = k_pad / TK, kk = OZ_S * k_pad;
+  const int nsplit = oz_splits(kseg);
+  auto blocks_for_rows = [&](size_t rows) {
+    return (int)std::max<size_t>(1, std::min<size_t>((rows + 7) / 8, (size_t)ex.sm_count * 16));
+  };
+  cudaEvent_t ev = nullptr;
+  if (ex.timing(tag)) ex.mark_begin(&ev);
+  DBuf<double> stA(ex.pool, ((size_t)g.batch * rowsA * kk * 2 + 7) / 8);
+  DBuf<double> stB(ex.pool, ((size_t)g.batch * rowsB * kk * 2 + 7) / 8);
+  DBuf<double> exA(ex.pool, ((size_t)g.batch * rowsA + 1) / 2), exB(ex.pool, ((size_t)g.batch * rowsB + 1) / 2);
+  auto* fA = reinterpret_cast<__nv_bfloat16*>(stA.p);
+  auto* fB = reinterpret_cast<__nv_bfloat16*>(stB.p);
+  int* eA = reinterpret_cast<int*>(exA.p);
+  int* eB = reinterpret_cast<int*>(exB.p);
+  oz_stage_kernel<<<blocks_for_rows((size_t)g.batch * rowsA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K,
+                                                                                  g.batch, rowsA, k_pad, 0, fA, eA);
+  ex.count();
+  oz_stage_kernel<<<blocks_for_rows((size_t)g.batch * rowsB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K,
+                                                                                  g.batch, rowsB, k_pad, 1, fB, eB);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+  CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM, true);
+  CUtensorMap mB = make_map(fB, kk, rowsB, g.batch, TN, true);
+  TcArgs a{};
+  a.M = g.M;
+  a.N = g.N;
+  a.kblocks = kk / TK;
+  a.num_m = rowsA / TM;
+  a.num_n = rowsB / TN;
+  a.batch = g.batch;
+  a.m_fast = a.num_m <= a.num_n ? 1 : 0;
+  a.splits = nsplit;
+  a.kchunk = OZ_NK;
+  a.oz_S = OZ_S;
+  a.oz_kseg = kseg;
+  a.oz_nk = OZ_NK;
+  const long long tiles = (long long)a.num_m * a.num_n * g.batch * nsplit;
+  CC_REQUIRE(tiles < (1LL << 31), CC_ERR_INVALID, "FP64-emulated contraction: too many tiles");
+  a.tiles = (int)tiles;
+  a.cm = g.cm;
+  a.cn = g.cn;
+  a.cb = g.cb;
+  a.alpha = g.alpha;
+  a.beta = g.beta;
+  a.C = g.C;
+  a.err = ex.dev_flag;
+  a.wait_ns = ex.wait_ns;
+  a.Cs = nullptr;
+  const size_t np = (size_t)nsplit * g.batch * g.M * g.N;
+  DBuf<double> part(ex.pool, (np + 1) / 2);
+  a.part = reinterpret_cast<float*>(part.p);
+  auto kern = gemm_tc_kernel<true, EPI_PART>;
+  static std::atomic<uint64_t> attr_done{0};
+  int dev = 0;
+  CC_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_done.load() & bit)) {
+    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    attr_done.fetch_or(bit);
+  }
+  kern<<<(int)std::min<long long>(tiles, ex.sm_count), THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+  // the fixed-point sum's bound: the level-L chunk sums add up to (L - 1) k_pad (2^beta - 1)^2
+  double bound = 0.0;
+  for (int L = 2; L <= OZ_S + 1; ++L)
+    bound += (L - 1) * (double)k_pad * (double)((1 << OZ_BETA) - 1) * ((1 << OZ_BETA) - 1) *
+             std::ldexp(1.0, OZ_BETA * (OZ_S + 1 - L));
+  const int gsh = std::max(0, (int)std::ceil(std::log2(bound)) - 61);
+  const size_t rows = (size_t)g.batch * g.M;
+  const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
+  const size_t items = rows * ((g.N + piece - 1) / piece);
+  const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
+  oz_combine_kernel<<<rblocks, 256, 0, ex.stream>>>(g, a.part, nsplit, kseg, gsh, eA, rowsA, eB, rowsB, piece);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+  if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
+}
+
 }  // namespace
 
 void k_wait_selftest(const Exec& ex) {
@@ -715,8 +955,8 @@ void k_wait_selftest(const Exec& ex) {
 }
 
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
-  CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3, CC_ERR_INVALID,
-             "tensor-core precision not available");
+  CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3 || prec == CC_FP64_EMU,
+             CC_ERR_INVALID, "tensor-core precision not available");
   CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
   if (g.K <= 0) {
     int blocks = (int)std::min<size_t>(((size_t)g.batch * g.M * g.N + 255) / 256, (size_t)ex.sm_count * 8);
@@ -727,8 +967,14 @@ void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* t
   }
   CC_REQUIRE((long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN) * g.batch < (1LL << 31), CC_ERR_INVALID,
              "tensor-core contraction: too many tiles");
-  if (prec == CC_MIXED_BF16X3) run_tc<true>(ex, prec, g, tag);
-  else run_tc<false>(ex, prec, g, tag);
+  if (prec == CC_FP64_EMU) {
+    CC_REQUIRE(!g.so && !g.sb, CC_ERR_INVALID, "staged operands need a single-precision tensor-core path");
+    run_oz(ex, g, tag);
+  } else if (prec == CC_MIXED_BF16X3) {
+    run_tc<true>(ex, prec, g, tag);
+  } else {
+    run_tc<false>(ex, prec, g, tag);
+  }
 }
 
 }  // namespace ccpnk

@@ -48,13 +48,15 @@ size_t footprint_bytes(int o, int v, int naux, const cc_solve_opts& op) {
   doubles += 3.0 * naux * n * n;                            // B (upload, blocks)
   doubles += 36.0 * oovv + 8.0 * naux * n * n;              // engine values + tangents
   doubles += 2.0 * lb * v * v * v;                          // ladder slab and its (c, d) split
-  if (op.prec != CC_FP64 && op.prec != CC_DF64) {           // its tensor-core staging copy,
+  if (op.prec != CC_FP64 && op.prec != CC_DF64 && op.prec != CC_FP64_EMU) {  // its tensor-core staging copy,
     doubles += std::ceil(lb * v / 256.0) * 256.0 * 3.0 * std::ceil((double)v * v / 64.0) * 64.0 / 2.0;
     doubles += ccpnk::stage_cache_cap(o, v, naux) / 8.0;    // and kept value-side operands
   }
   doubles += (op.m_max + 8.0) * namp;                       // outer Krylov basis and vectors
   doubles += (op.af_direct ? 2.0 : (op.inner_max + 2.0)) * namp;  // A_F inverse work
   doubles += 4.0 * oovv;                                    // split-k partials, staging
+  if (op.prec == CC_FP64_EMU || op.outer_prec == CC_FP64_EMU)  // digit slices and exact partial sums
+    doubles += 2.0 * lb * v * v * v + 8.0 * naux * v * v;
   return (size_t)(doubles * 8.0 * 1.15) + (64u << 20);
 }
 

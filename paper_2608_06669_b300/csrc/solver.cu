@@ -280,7 +280,7 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
       k_axpby(ex, n - n1, 0.5, symw.p, 0.0, x + n1);
     }
   };
-  const cc_precision outer = opt.outer_prec == CC_DF64 ? CC_DF64 : CC_FP64;
+  const cc_precision outer = opt.outer_prec == CC_DF64 ? CC_DF64 : opt.outer_prec == CC_FP64_EMU ? CC_FP64_EMU : CC_FP64;
   auto out_of_time = [&]() {
     return opt.max_seconds > 0 &&
            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > opt.max_seconds;

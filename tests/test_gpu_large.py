@@ -7,8 +7,11 @@ that smaller cases never reach. Small o and naux keep the oracle's cost at secon
 v-dependent paths run at full size. The o=20 v=180 naux=600 workload itself is compared in
 full (FP64 residual and energy per element), once.
 
-Tolerances as in the other parity tests: 1e-10 normwise-elementwise for FP64, 1e-6 for the
-three-pass TF32 split, 2e-5 for the three-pass BF16 split.
+Tolerances: 1e-10 normwise-elementwise for FP64 (and its tensor-core emulation), 2e-5 for the
+three-pass BF16 split, and 5e-6 for the three-pass TF32 split: each product keeps all but about
+3 * 2^-22 of its value (the dropped lo * lo term and the two splitting remainders), and the FP32
+accumulation over the ladder's v^2 (about 3e4 to 7e4) terms adds to that; up to 1.9e-6 is
+observed at v = 180.
 """
 import numpy as np
 import pytest
@@ -57,12 +60,15 @@ def test_ladder_block_sizes_cover_the_capped_branch():
 
 @pytest.mark.parametrize("o,v,naux", [(2, 180, 8), (2, 240, 6), (2, 270, 6)])
 def test_fp64_residual_large_v(ctx, o, v, naux):
+    """FP64 and its tensor-core emulation (CC_FP64_EMU) at the FP64 bound."""
     s = synth.make_system(o, v, naux, seed=300 + v, gauge="haar")
     t1, t2 = synth.random_amplitudes(np.random.default_rng(v), o, v, 0.05, 0.05)
-    r1, r2, e = gsys(ctx, s).residual(t1, t2)
     q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
-    assert nerr((r1, r2), (q1, q2)) <= TOL64
-    assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
+    g = gsys(ctx, s)
+    for prec in ("fp64", "fp64emu"):
+        r1, r2, e = g.residual(t1, t2, prec=prec)
+        assert nerr((r1, r2), (q1, q2)) <= TOL64, prec
+        assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
 
 
 @pytest.mark.parametrize("o,v,naux", [(1, 240, 4), (2, 270, 4)])
@@ -76,7 +82,7 @@ def test_fp64_jvp_large_v(ctx, o, v, naux):
     assert nerr(j, q) <= TOL64
 
 
-@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-6), ("bf16x3", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 5e-6), ("bf16x3", 2e-5)])
 @pytest.mark.parametrize("v", [180, 270])
 def test_mixed_residual_and_jvp_large_v(ctx, prec, tol, v):
     o, naux = 2, 6
@@ -99,7 +105,9 @@ def test_fp64_residual_near_degenerate_workload(ctx):
     s = synth.workload("o20v180_neardegenerate")
     o, v = s.o, s.v
     t1, t2 = synth.random_amplitudes(np.random.default_rng(17), o, v, 0.01, 0.01)
-    r1, r2, e = gsys(ctx, s).residual(t1, t2)
     q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
-    assert nerr((r1, r2), (q1, q2)) <= TOL64
-    assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
+    g = gsys(ctx, s)
+    for prec in ("fp64", "fp64emu"):
+        r1, r2, e = g.residual(t1, t2, prec=prec)
+        assert nerr((r1, r2), (q1, q2)) <= TOL64, prec
+        assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))

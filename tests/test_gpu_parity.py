@@ -305,3 +305,53 @@ def test_mp2_start_with_singles_driving_term(ctx):
     q1, q2 = cc.mp2_guess(s.fock, s.B, o)
     assert np.abs(q1).max() > 1e-3
     assert rel_err(t1, q1) <= TOL64 and rel_err(t2, q2) <= TOL64
+
+
+@pytest.mark.parametrize("o,v,naux,gauge", [(1, 1, 1, "canonical"), (2, 3, 4, "haar"), (4, 9, 11, "haar"),
+                                             (7, 33, 20, "haar"), (5, 70, 40, "small")])
+def test_fp64_emulated_residual_and_jvp_parity(ctx, o, v, naux, gauge):
+    """CC_FP64_EMU (Ozaki slices on the tensor cores, exact FP32 chunk sums, integer recombination)
+    meets the FP64 bound element by element, on the residual and on the JVP."""
+    s = synth.make_system(o, v, naux, seed=200 + o * v, gauge=gauge)
+    rng = np.random.default_rng(o + 2 * v)
+    t1, t2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    d1, d2 = synth.random_amplitudes(rng, o, v, 0.1, 0.1)
+    g = gpu_system(ctx, s)
+    r1, r2, e = g.residual(t1, t2, prec="fp64emu")
+    q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
+    scale = max(np.abs(q1).max(), np.abs(q2).max())
+    assert np.abs(r1 - q1).max() <= TOL64 * scale and np.abs(r2 - q2).max() <= TOL64 * scale
+    assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
+    j1, j2 = g.jvp(t1, t2, d1, d2, prec="fp64emu")
+    p1, p2 = cc.jvp(s.fock, s.B, o, t1, t2, d1, d2)
+    scale = max(np.abs(p1).max(), np.abs(p2).max())
+    assert np.abs(j1 - p1).max() <= TOL64 * scale and np.abs(j2 - p2).max() <= TOL64 * scale
+
+
+def test_fp64_emulated_workload_residual(ctx):
+    s = synth.workload("o10v90_rotated")
+    o, v = s.o, s.v
+    t1, t2 = cc.mp2_guess(s.fock, s.B, o)
+    p1, p2 = synth.random_amplitudes(np.random.default_rng(3), o, v, 0.01, 0.01)
+    t1, t2 = t1 + p1, t2 + p2
+    r1, r2, e = gpu_system(ctx, s).residual(t1, t2, prec="fp64emu")
+    q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
+    scale = max(np.abs(q1).max(), np.abs(q2).max())
+    assert np.abs(r1 - q1).max() <= TOL64 * scale and np.abs(r2 - q2).max() <= TOL64 * scale
+    assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
+
+
+@pytest.mark.parametrize("prec", ["fp64emu", "tf32x3"])
+def test_pnk_with_emulated_outer_residual(ctx, prec):
+    """PNK with the outer residual (convergence test, energy) in CC_FP64_EMU lands on the oracle
+    root within 1e-8 Eh, and its amplitudes zero the oracle residual."""
+    for name in ("o5v20_canonical", "o10v90_rotated"):
+        s = synth.workload(name)
+        ref = _golden()[name]["e_corr"]
+        t1, t2, rep = gpu_system(ctx, s).solve("pnk", prec, af_direct=1, outer_prec=5)
+        assert rep["status_code"] == 0, (name, rep)
+        assert abs(rep["energy"] - ref) < 1e-8, name
+        if name == "o5v20_canonical":
+            q1, q2, eq = cc.residual(s.fock, s.B, s.o, t1, t2)
+            assert np.sqrt((q1 ** 2).sum() + (q2 ** 2).sum()) < 1e-8 and abs(eq - rep["energy"]) < 1e-10
+
