@@ -34,10 +34,6 @@ METRIC = "PNK time-to-‖R‖<1e-8, mixed vs FP64; residual TFLOP/s vs peak; p50
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # TF32 dense tensor peak: measured bf16 burst x the nominal TF32/BF16 ratio (1.1 / 2.25)
 TF32_RATIO = 1.1 / 2.25
-# DRAM bytes (read + write) per FP64 ladder-build launch, averaged over the eight build launches
-# of one FP64 residual at o=10, v=90, naux=300, from one ncu capture of the current kernel
-# (the FP64 ladder-build summary among the kernel profiles); the slab it writes mostly stays in L2
-LADDER_BUILD_F64_DRAM_BYTES = 12.65e6
 
 
 def rank_info():
@@ -241,6 +237,142 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def roofline_entry(rec, kind, peaks, peak_kind):
+    """Roofline of one tagged GEMM from the kernel timer's (launches, ms, flops) record. kind:
+    'fp64' (FMA pipe), 'tf32x3' (three TF32 passes on tcgen05), 'emu' (Ozaki slices: 36 BF16
+    slice products per FP64-equivalent product on tcgen05 kind::f16)."""
+    n, ms, fl = rec
+    if not n or ms <= 0:
+        return None
+    if kind == "fp64":
+        ach, peak = fl / (ms / 1e3) / 1e12, FP64_PEAK_TFLOPS
+        return {"bound": "alu", "kernel": "gemm_f64_kernel (FP64 ladder build, FMA pipe)", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches": n, "ms_per_launch": ms / n,
+                "flops_per_launch": fl / n, "peak_source": "148 SMs x 2 DFMA/clk x 2 x 2.032 GHz (unit counts)"}
+    if kind == "tf32x3":
+        peak = peaks["bf16_tflops"] * TF32_RATIO
+        ach = 3.0 * fl / (ms / 1e3) / 1e12
+        return {"bound": "tensor", "kernel": "gemm_tc_kernel<tf32> (ladder build of the JVP, three TF32 passes)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches": n,
+                "ms_per_launch": ms / n, "flops_per_launch": 3.0 * fl / n, "logical_tflops": fl / (ms / 1e3) / 1e12,
+                "peak_source": f"{peak_kind} bf16 burst x 1.1/2.25 (of {peak_kind})"}
+    peak = peaks["bf16_tflops"]
+    ach = 36.0 * fl / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "FP64-emulated ladder build: oz_rowexp/oz_digits staging, "
+                                         "gemm_tc_kernel<bf16, partials>, oz_combine",
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches": n,
+            "ms_per_launch": ms / n, "flops_per_launch": 36.0 * fl / n,
+            "fp64_equivalent_tflops": fl / (ms / 1e3) / 1e12,
+            "peak_source": f"{peak_kind} bf16 burst (of {peak_kind}); achieved counts the 36 BF16 slice products "
+                           f"of each FP64-equivalent product, time covers staging, MMA and the combine"}
+
+
+def timed(fn):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, r
+
+
+def large_block(args, peaks, peak_kind):
+    """The o=30, v=270, naux=900 workload: FP64 residual natively and emulated on the tensor
+    cores, the mixed JVPs, ladder rates against their peaks, and capped Newton steps of the
+    mixed PNK solve (the workload is outside the range where any method converges; see the
+    convergence study), one JVP of the native FP64 path for the FP64 per-step cost."""
+    import numpy as np
+    import torch
+
+    from paper_2608_06669_b300 import ccpnk, synth
+
+    s = synth.workload("o30v270_rotated")
+    o, v = s.o, s.v
+    ctx = ccpnk.Context(0)
+    g = ccpnk.System.from_synth(ctx, s)
+    rng = np.random.default_rng(0)
+    t1, t2 = synth.random_amplitudes(rng, o, v, 0.01, 0.01)
+    T1, T2 = torch.from_numpy(t1).cuda(), torch.from_numpy(t2).cuda()
+    out = {"workload": "o30v270_rotated", "o": o, "v": v, "naux": s.naux}
+    ctx.profile(True)
+    out["fp64emu_residual_s"], (_, _, e_emu) = timed(lambda: g.residual(T1, T2, prec="fp64emu"))
+    out["ladder_build_fp64emu"] = roofline_entry(ctx.profile_get("ladder_build.emu"), "emu", peaks, peak_kind)
+    if not args.no_fp64_large:
+        ctx.profile(True)
+        out["fp64_residual_s"], (_, _, e64) = timed(lambda: g.residual(T1, T2, prec="fp64"))
+        out["ladder_build_fp64"] = roofline_entry(ctx.profile_get("ladder_build.fp64"), "fp64", peaks, peak_kind)
+        out["emu_vs_fp64_energy_diff"] = e_emu - e64
+        out["fp64emu_residual_speedup"] = out["fp64_residual_s"] / out["fp64emu_residual_s"]
+    for prec in ("tf32x3", "bf16x3"):
+        ctx.profile(True)
+        dt, _ = timed(lambda: g.jvp(T1, T2, T1, T2, prec=prec))
+        out[f"{prec}_jvp_incl_fp64emu_value_s"] = dt
+        sfx = "bf16" if prec == "bf16x3" else "tf32"
+        n, ms, fl = ctx.profile_get(f"ladder_build.{sfx}")
+        out[f"{prec}_ladder_build_logical_tflops"] = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+        if prec == "tf32x3":
+            out["ladder_build_tf32x3"] = roofline_entry((n, ms, fl), "tf32x3", peaks, peak_kind)
+    ctx.profile(False)
+    steps = args.large_newton
+    dt, (_, _, rep) = timed(lambda: g.solve("pnk", "tf32x3", af_direct=1, outer_prec=5, max_outer=steps))
+    out["mixed_pnk_newton_steps"] = {"steps": rep["newton_iters"], "seconds": dt,
+                                     "s_per_newton_step": dt / max(rep["newton_iters"], 1), "jvps": rep["jvps"],
+                                     "res_norm": rep["res_norm"], "energy": rep["energy"]}
+    dt, (_, _, rep) = timed(lambda: g.solve("pnk", "fp64emu", af_direct=1, outer_prec=5, max_outer=steps))
+    out["fp64emu_pnk_newton_steps"] = {"steps": rep["newton_iters"], "seconds": dt,
+                                       "s_per_newton_step": dt / max(rep["newton_iters"], 1), "jvps": rep["jvps"],
+                                       "res_norm": rep["res_norm"]}
+    if args.fp64_large_jvp:
+        dt, _ = timed(lambda: g.jvp(T1, T2, T1, T2, prec="fp64"))
+        out["fp64_jvp_incl_fp64_value_s"] = dt
+    g.close()
+    ctx.close()
+    return out
+
+
+def served_block(args):
+    """The first --serve-default requests of the served mix, submitted at their Poisson arrival
+    times to the continuous-batching server, once on the mixed path and once on the FP64 path
+    (the same requests): p50/p99 time to solution, solves/s and convergence."""
+    import numpy as np
+
+    from paper_2608_06669_b300 import ccpnk, synth
+
+    reqs = synth.served_requests(args.serve_default)
+    out = {"requests": len(reqs), "slots": args.slots, "arrivals": "exponential, mean 20 ms"}
+    for key, prec, extra in (("mixed", "tf32x3", {"outer_prec": 5}), ("fp64", "fp64", {})):
+        srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=args.slots)
+        t_start = time.perf_counter()
+        tickets = []
+        for arrival, sy in reqs:
+            wait = arrival - (time.perf_counter() - t_start)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(srv.submit(sy.o, sy.v, sy.naux, sy.fock, sy.B, "pnk", prec, af_direct=1,
+                                      max_outer=args.max_newton, max_seconds=args.solve_seconds, **extra))
+        results = {}
+        while len(results) < len(tickets):
+            for t in tickets:
+                if t not in results:
+                    r = srv.poll(t)
+                    if r is not None:
+                        results[t] = r
+            time.sleep(0.002)
+        times = [srv.times(t) for t in tickets]
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([f - sub for sub, _, f in times])
+        span = max(f for _, _, f in times) - min(sub for sub, _, _ in times)
+        conv = [results[t][2]["status_code"] == 0 for t in tickets]
+        out[key] = {"solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
+                    "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(conv)), "makespan_s": span,
+                    "max_concurrent": stats["max_running"],
+                    "not_converged": [f"o{sy.o}v{sy.v}" for (_, sy), c in zip(reqs, conv) if not c],
+                    "outer_residual": "fp64emu" if key == "mixed" else "fp64"}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -265,8 +397,9 @@ def run_ours(args):
     g = ccpnk.System.from_synth(ctx, s)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
-    # A_F^{-1} exactly in the Fock eigenbasis; the paper's inner-GMRES inversion is timed beside it
-    kw = dict(method="pnk", prec=args.prec, af_direct=0 if args.af_gmres else 1)
+    # JVPs and A_F^{-1} in the mixed precision, the outer residual (convergence test, energy) in
+    # FP64 emulated on the tensor cores, A_F^{-1} exactly in the Fock eigenbasis
+    kw = dict(method="pnk", prec=args.prec, af_direct=0 if args.af_gmres else 1, outer_prec=args.outer)
 
     for _ in range(args.warmup):
         g.solve(**kw)
@@ -288,8 +421,8 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1) / 1e3)
             reports.append(rep)
     launches = ctx.launches - launches0
-    lb = ctx.profile_get("ladder_build.fp64")
-    lc = ctx.profile_get("ladder_build.tf32")
+    tags = {"fp64": ctx.profile_get("ladder_build.fp64"), "emu": ctx.profile_get("ladder_build.emu"),
+            "tf32x3": ctx.profile_get("ladder_build.tf32")}
     ctx.profile(False)
     t_mean = statistics.mean(times)
     t_max = t_mean
@@ -298,32 +431,29 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
 
-    # FP64 PNK on the same workload (the mixed path must beat it)
-    t0 = time.perf_counter()
-    _, _, rep64 = g.solve(method="pnk", prec="fp64", af_direct=kw["af_direct"])
-    t_fp64 = time.perf_counter() - t0
-    # the same mixed solve with A_F inverted by inner GMRES (the paper's protocol)
-    t0 = time.perf_counter()
-    _, _, rep_gm = g.solve(method="pnk", prec=args.prec, af_direct=0)
-    t_gmres = time.perf_counter() - t0
-
-    # the same solves with the outer residual in double-float (FP32 pairs on the FP32 pipe),
-    # and a solve done entirely in double-float
-    t0 = time.perf_counter()
-    _, _, rep_df = g.solve(method="pnk", prec=args.prec, af_direct=kw["af_direct"], outer_prec=4)
-    t_df_outer = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    _, _, rep_dfall = g.solve(method="pnk", prec="df64", af_direct=kw["af_direct"], outer_prec=4)
-    t_df_all = time.perf_counter() - t0
-    # the inner contractions as three BF16 passes (kind::f16) instead of three TF32 passes
-    t0 = time.perf_counter()
-    _, _, rep_bf = g.solve(method="pnk", prec="bf16x3", af_direct=kw["af_direct"], outer_prec=4)
-    t_bf = time.perf_counter() - t0
+    # the same mixed solve with a native FP64 outer residual, the native FP64 PNK (the mixed
+    # path must beat it), PNK with every contraction FP64-emulated, the inner-GMRES A_F^{-1}
+    # (the paper's protocol), and the double-float variants
+    variants = {
+        "mixed_pnk_fp64_outer": dict(method="pnk", prec=args.prec, af_direct=1),
+        "fp64_pnk": dict(method="pnk", prec="fp64", af_direct=1),
+        "fp64emu_pnk": dict(method="pnk", prec="fp64emu", af_direct=1, outer_prec=5),
+        "mixed_pnk_af_gmres": dict(method="pnk", prec=args.prec, af_direct=0, outer_prec=args.outer),
+        "mixed_pnk_bf16x3": dict(method="pnk", prec="bf16x3", af_direct=1, outer_prec=args.outer),
+        "mixed_pnk_df64_outer": dict(method="pnk", prec=args.prec, af_direct=1, outer_prec=4),
+        "df64_pnk": dict(method="pnk", prec="df64", af_direct=1, outer_prec=4),
+    }
+    if args.only_headline:
+        variants = {}
+    var_out = {}
+    for name, vkw in variants.items():
+        dt, (_, _, rep) = timed(lambda: g.solve(**vkw))
+        var_out[name] = {"s": dt, **{k: rep[k] for k in ("energy", "res_norm", "newton_iters", "jvps", "status_code")}}
 
     # end to end through the C ABI with host buffers: upload the problem, solve, read back
     n = s.o + s.v
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(0 if args.only_headline else max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         gh = ccpnk.System(ctx, s.o, s.v, s.naux, s.fock, s.B)
@@ -333,53 +463,48 @@ def run_ours(args):
         gh.close()
     h2d = 8 * (n * n + s.naux * n * n)
     d2h = 8 * (s.o * s.v + s.o ** 2 * s.v ** 2)
+    g.close()
+    ctx.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    # roofline of the dominant kernel: the FP64 ladder build (2 naux v^4 flops per launch)
-    ach = lb[2] / (lb[1] / 1e3) / 1e12 if lb[1] > 0 else None
-    roof = {"bound": "alu", "kernel": "gemm_f64_kernel (ladder build, FP64 FMA pipe)", "achieved": ach,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": (ach / FP64_PEAK_TFLOPS) if ach else None,
-            "traffic": LADDER_BUILD_F64_DRAM_BYTES, "launches": lb[0], "ms_per_launch": lb[1] / max(lb[0], 1),
-            "flops_per_launch": lb[2] / max(lb[0], 1), "peak_source": "148 SMs x 2 DFMA/clk x 2 x 2.032 GHz"}
-    tf32_peak = peaks["bf16_tflops"] * TF32_RATIO
-    ach_tc = lc[2] / (lc[1] / 1e3) / 1e12 if lc[1] > 0 else None
-    roof_tc = {"bound": "tensor", "kernel": "gemm_tc_kernel (ladder build, tcgen05 kind::tf32, three-pass split)", "achieved": ach_tc,
-               "peak": tf32_peak, "unit": "TFLOP/s", "frac": (ach_tc / tf32_peak) if ach_tc else None,
-               "launches": lc[0], "peak_source": f"{peak_kind} bf16 burst x 1.1/2.25"}
+    # rooflines of the timed solve's ladder GEMMs; the dominant one (most event time) is the line's
+    roofs = {k: roofline_entry(tags[k], k, peaks, peak_kind) for k in tags}
+    roofs = {k: r for k, r in roofs.items() if r}
+    dom = max(roofs, key=lambda k: tags[k][1]) if roofs else None
+    roof = dict(roofs[dom]) if dom else None
+    if roof:
+        roof["traffic"] = None  # DRAM bytes of this kernel come from the ncu summaries in profiles/
+        roof["share_of_timed_solve"] = tags[dom][1] / 1e3 / (t_max * args.steps)
     cpu = None
-    if world == 1 and not args.no_cpu:
+    if world == 1 and not args.no_cpu and not args.only_headline:
         cpu = cpu_baseline()
-    res_flops = 2 * s.naux * s.v ** 4 + 2 * s.o ** 2 * s.v ** 4
+    extra = world == 1 and not args.only_headline
+    large = large_block(args, peaks, peak_kind) if (extra and not args.no_large) else None
+    served = served_block(args) if (extra and args.serve_default > 0) else None
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"tf32x3": "tf32x3+f64", "bf16x3": "bf16x3+f64", "tf32": "tf32+f64", "fp64": "f64"}[args.prec], "data": "synthetic",
+        "dtype": f"{args.prec} JVPs + {'fp64emu' if args.outer == 5 else 'f64'} outer residual", "data": "synthetic",
         "config": {"workload": WORKLOAD, "o": s.o, "v": s.v, "naux": s.naux, "gauge": "rotated (off-diagonal f up to 0.1 Eh)",
-                   "method": "pnk", "prec": args.prec, "tol": 1e-8, "start": "generalised MP2",
-                   "af_inverse": "gmres" if args.af_gmres else "eigenbasis",
+                   "method": "pnk", "prec": args.prec, "outer_residual": "fp64emu" if args.outer == 5 else "fp64",
+                   "tol": 1e-8, "start": "generalised MP2", "af_inverse": "gmres" if args.af_gmres else "eigenbasis",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "roofline": roof, "roofline_tensor": roof_tc,
+        "roofline": roof, "rooflines": roofs,
         "cpu_baseline": cpu,
-        "e2e": {"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": statistics.mean(e2e_times) if e2e_times else None, "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // max(args.steps, 1),
         "clocks": clk.summary(),
-        "fp64_pnk_s": t_fp64,
-        "speedup_mixed_vs_fp64": t_fp64 / t_max,
-        "mixed_pnk_af_gmres_s": t_gmres,
-        "mixed_pnk_df64_outer_s": t_df_outer,
-        "df64_pnk_s": t_df_all,
-        "solve_df64_outer": {k: rep_df[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
-        "solve_df64": {k: rep_dfall[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
-        "mixed_pnk_bf16x3_df64_outer_s": t_bf,
-        "solve_bf16x3_df64_outer": {k: rep_bf[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
-        "solve_af_gmres": {k: rep_gm[k] for k in ("energy", "res_norm", "newton_iters", "jvps", "af_applies")},
+        "fp64_pnk_s": var_out["fp64_pnk"]["s"] if var_out else None,
+        "speedup_mixed_vs_fp64": var_out["fp64_pnk"]["s"] / t_max if var_out else None,
+        "variants": var_out,
         "solve": {k: reports[-1][k] for k in ("energy", "res_norm", "newton_iters", "residual_evals", "jvps",
                                                "af_applies", "krylov_iters")},
-        "solve_fp64": {k: rep64[k] for k in ("energy", "res_norm", "newton_iters", "jvps")},
-        "ladder_flops_per_residual": res_flops,
+        "large": large,
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -594,7 +719,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "bf16x3", "tf32", "fp64"])
+    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "bf16x3", "tf32", "fp64", "fp64emu"])
+    ap.add_argument("--outer", type=int, default=5, help="outer-residual precision code (0 FP64, 4 DF64, 5 FP64-emulated)")
+    ap.add_argument("--no-large", action="store_true", help="skip the o=30 v=270 block of the main line")
+    ap.add_argument("--no-fp64-large", action="store_true", help="skip the native FP64 residual/JVP at o=30 v=270")
+    ap.add_argument("--large-newton", type=int, default=2, help="capped Newton steps at o=30 v=270")
+    ap.add_argument("--fp64-large-jvp", action="store_true", help="also time one native FP64 JVP at o=30 v=270")
+    ap.add_argument("--serve-default", type=int, default=32, help="requests of the served block (0: skip)")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="only the timed solves (the launch-list and profile captures run this)")
     ap.add_argument("--af-gmres", action="store_true", help="invert A_F by inner GMRES in the timed solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-iterations", type=int, default=3, help="oracle iterations per reference step")

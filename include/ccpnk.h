@@ -175,7 +175,9 @@ int cc_residual(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
                 double* r1, double* r2, double* energy, cc_precision prec);
 
 /* J(t) d, the exact directional derivative of R at t along d (App. B: every bilinear
- * contraction becomes two). Mixed precisions run the contractions on tensor cores. */
+ * contraction becomes two). Mixed precisions run the contractions on tensor cores; the
+ * intermediates at t that the derivative multiplies are computed in FP64 for prec = CC_FP64 or
+ * CC_DF64, and in the FP64 emulation (CC_FP64_EMU) otherwise. */
 int cc_jvp(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2,
            const double* d1, const double* d2, double* j1, double* j2, cc_precision prec);
 

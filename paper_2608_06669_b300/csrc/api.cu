@@ -190,6 +190,12 @@ void check_prec(cc_precision p) {
              CC_ERR_INVALID, "unknown precision");
 }
 
+// Precision of the value-side intermediates a JVP linearises around: FP64 for the FP64 and
+// double-float JVPs, the tensor-core FP64 emulation (FP64-accurate) for the other precisions.
+cc_precision value_prec(cc_precision prec) {
+  return prec == CC_FP64 || prec == CC_DF64 ? CC_FP64 : CC_FP64_EMU;
+}
+
 // [t1 | t2] with t2 symmetrised: T2 only depends on t_ij^ab + t_ji^ba
 void load_amplitudes(cc_ctx* ctx, const System& s, const double* t1, const double* t2, double* dst) {
   const size_t ov = (size_t)s.o * s.v;
@@ -416,7 +422,7 @@ int cc_jvp(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2, const d
     DBuf<double> t(ex.pool, s.namp()), d(ex.pool, s.namp()), r(ex.pool, s.namp());
     load_amplitudes(ctx, s, t1, t2, t.p);
     load_amplitudes(ctx, s, d1, d2, d.p);
-    eng.value(t.p, r.p, nullptr, CC_FP64);
+    eng.value(t.p, r.p, nullptr, value_prec(prec));
     eng.tangent(d.p, r.p, prec);
     const size_t ov = (size_t)s.o * s.v;
     copy_out(ctx, j1, r.p, ov);
@@ -439,7 +445,7 @@ int cc_jvp_multi(cc_ctx* ctx, cc_sys* sys, const double* t1, const double* t2, i
     const size_t ov = (size_t)s.o * s.v, oovv = s.namp() - ov;
     DBuf<double> t(ex.pool, s.namp()), d(ex.pool, s.namp()), r(ex.pool, s.namp());
     load_amplitudes(ctx, s, t1, t2, t.p);
-    eng.value(t.p, r.p, nullptr, CC_FP64);
+    eng.value(t.p, r.p, nullptr, value_prec(prec));
     for (int k = 0; k < ndir; ++k) {
       load_amplitudes(ctx, s, d1s + k * ov, d2s + k * oovv, d.p);
       eng.tangent(d.p, r.p, prec);

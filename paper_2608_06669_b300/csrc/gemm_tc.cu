@@ -200,40 +200,65 @@ constexpr int OZ_S = 8;      // slices per operand: 48 significant bits
 constexpr int OZ_BETA = 6;   // bits per slice digit
 constexpr int OZ_NK = 16;    // k blocks (of 64) per exact FP32 chunk: 16 * 64 * 63^2 < 2^22
 
-// One warp per staged row: pass 1 finds the largest exponent of the row, pass 2 writes the
-// S digit slices of every element as BF16 into the K-major staging layout
-// out[b][r][seg * k_pad + k] (segment s - 1 holds slice s for A; B holds slice t in segment
-// S - t), zeros outside rows x K. expo[b * rows_pad + r] = sigma. The digits come from the
-// FP64 bit pattern with integer shifts (no FP64 arithmetic).
-__global__ void oz_stage_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
-                                int batch, int rows_pad, int k_pad, int rev, __nv_bfloat16* __restrict__ out,
-                                int* __restrict__ expo) {
+// Pass 1 of the digit staging: the largest biased exponent of every staged row (a row of A or
+// a column of B), one warp per piece of ROW_PIECE elements of a row, combined by an integer
+// atomicMax (order-independent). emax must start at 0; a row of zeros keeps 0.
+__global__ void oz_rowexp_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
+                                 int batch, int rows_pad, unsigned* __restrict__ emax) {
   const int lane = threadIdx.x & 31;
-  const long long items = (long long)batch * rows_pad;
+  const int pieces = (K + ROW_PIECE - 1) / ROW_PIECE;
+  const long long items = (long long)batch * rows * pieces;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = w0; it < items; it += nw) {
+    const long long q = it / pieces;  // real row b * rows + r
+    const int k0 = (int)(it - q * pieces) * ROW_PIECE, k1 = min(K, k0 + ROW_PIECE);
+    const int b = (int)(q / rows), r = (int)(q - (long long)b * rows);
+    const double* srow = src + cidx(bix, b) + cidx(rix, r);
+    unsigned e = 0;
+    CWalk kw;
+    kw.init(kix, k0 + lane);
+    for (int k = k0 + lane; k < k1; k += 32) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
+      e = max(e, (unsigned)((bits >> 52) & 0x7FF));
+      kw.step(kix, 32);
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (lane == 0 && e) atomicMax(emax + (size_t)b * rows_pad + r, e);
+  }
+}
+
+// Pass 2: the S digit slices of every element as BF16 in the K-major staging layout
+// out[b][r][seg * k_pad + k] (segment s - 1 holds slice s for A; B holds slice t in segment
+// S - t), zeros outside rows x K; one warp per piece of a staged row. With the row's exponent
+// sigma = max(emax, 1) - 1022 (every |x| of the row is below 2^sigma), the digits come from the
+// FP64 bit pattern by integer shifts (no FP64 arithmetic).
+__global__ void oz_digits_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
+                                 int batch, int rows_pad, int k_pad, int rev, const unsigned* __restrict__ emax,
+                                 __nv_bfloat16* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int pieces = (k_pad + ROW_PIECE - 1) / ROW_PIECE;
+  const long long items = (long long)batch * rows_pad * pieces;
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const size_t row_len = (size_t)OZ_S * k_pad;
-  for (long long q = w0; q < items; q += nw) {
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  for (long long it = w0; it < items; it += nw) {
+    const long long q = it / pieces;  // staged row b * rows_pad + r
+    const int k0 = (int)(it - q * pieces) * ROW_PIECE, k1 = min(k_pad, k0 + ROW_PIECE);
     const int b = (int)(q / rows_pad), r = (int)(q - (long long)b * rows_pad);
     __nv_bfloat16* row = out + (size_t)q * row_len;
     if (r >= rows) {
-      for (size_t k = lane; k < row_len; k += 32) row[k] = __float2bfloat16_rn(0.0f);
-      if (lane == 0) expo[q] = 0;
+      for (int k = k0 + lane; k < k1; k += 32)
+#pragma unroll
+        for (int sl = 0; sl < OZ_S; ++sl) row[(size_t)sl * k_pad + k] = zero;
       continue;
     }
+    const unsigned em = max(emax[q], 1u);
     const double* srow = src + cidx(bix, b) + cidx(rix, r);
-    unsigned emax = 1;  // biased exponent; 1 also covers zeros and subnormals
     CWalk kw;
-    kw.init(kix, lane);
-    for (int k = lane; k < K; k += 32) {
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
-      emax = max(emax, (unsigned)((bits >> 52) & 0x7FF));
-      kw.step(kix, 32);
-    }
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    if (lane == 0) expo[q] = (int)emax - 1022;  // every |x| of the row is below 2^(emax - 1022)
-    kw.init(kix, lane);
-    for (int k = lane; k < k_pad; k += 32) {
+    kw.init(kix, k0 + lane);
+    for (int k = k0 + lane; k < k1; k += 32) {
       unsigned long long qv = 0, neg = 0;
       if (k < K) {
         const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
@@ -242,10 +267,9 @@ __global__ void oz_stage_kernel(const double* __restrict__ src, CIdx rix, CIdx k
         if (e) m |= 1ull << 52;
         else e = 1;
         neg = bits >> 63;
-        // |x| = m 2^(e - 1075); in units of 2^(sigma - beta S): m >> (emax - e + 53 - beta S)
-        const unsigned sh = emax - e + 53 - OZ_BETA * OZ_S;
+        // |x| = m 2^(e - 1075); in units of 2^(sigma - beta S): m >> (em - e + 53 - beta S)
+        const unsigned sh = em - e + 53 - OZ_BETA * OZ_S;
         qv = sh >= 64 ? 0ull : (m >> sh);
-        kw.step(kix, 32);
       }
 #pragma unroll
       for (int sl = 1; sl <= OZ_S; ++sl) {
@@ -254,6 +278,7 @@ __global__ void oz_stage_kernel(const double* __restrict__ src, CIdx rix, CIdx k
         const int seg = rev ? OZ_S - sl : sl - 1;
         row[(size_t)seg * k_pad + k] = __float2bfloat16_rn(f);
       }
+      kw.step(kix, 32);
     }
   }
 }
@@ -262,8 +287,8 @@ __global__ void oz_stage_kernel(const double* __restrict__ src, CIdx rix, CIdx k
 // per piece of an output row; the chunk sums are integers below 2^22, added per level in int64
 // and combined in 64-bit fixed point with the levels' scales 2^(OZ_BETA (S + 1 - L) - gsh)
 // (gsh > 0 drops low bits of the smallest levels so that the sum stays below 2^62).
-__global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, int nsplit, int kseg, int gsh,
-                                  const int* __restrict__ expA, int rowsA_pad, const int* __restrict__ expB,
+__global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, int kseg, int gsh,
+                                  const unsigned* __restrict__ expA, int rowsA_pad, const unsigned* __restrict__ expB,
                                   int rowsB_pad, int piece) {
   const int lane = threadIdx.x & 31;
   const size_t tot = (size_t)g.batch * g.M * g.N;
@@ -277,7 +302,7 @@ __global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, in
     const int b = (int)(qrow / g.M), m = (int)(qrow - (long long)b * g.M);
     const long long rowoff = cidx(g.cb, b) + cidx(g.cm, m);
     const float* pr = part + (size_t)qrow * g.N;
-    const int ea = expA[(size_t)b * rowsA_pad + m];
+    const int ea = (int)max(expA[(size_t)b * rowsA_pad + m], 1u) - 1022;  // sigma of row m
     CWalk cw;
     cw.init(g.cn, n0 + lane);
     for (int n = n0 + lane; n < n1; n += 32) {
@@ -290,8 +315,8 @@ __global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, in
         const int sh = OZ_BETA * (OZ_S + 1 - L) - gsh;
         acc += sh >= 0 ? (lv << sh) : ((lv + (1ll << (-sh - 1))) >> (-sh));
       }
-      (void)nsplit;
-      const int e = ea + expB[(size_t)b * rowsB_pad + n] - OZ_BETA * (OZ_S + 1) + gsh;
+      const int eb = (int)max(expB[(size_t)b * rowsB_pad + n], 1u) - 1022;
+      const int e = ea + eb - OZ_BETA * (OZ_S + 1) + gsh;
       const double val = g.alpha * ldexp((double)acc, e);
       double* c = g.C + rowoff + cw.off;
       *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
@@ -878,14 +903,23 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   DBuf<double> exA(ex.pool, ((size_t)g.batch * rowsA + 1) / 2), exB(ex.pool, ((size_t)g.batch * rowsB + 1) / 2);
   auto* fA = reinterpret_cast<__nv_bfloat16*>(stA.p);
   auto* fB = reinterpret_cast<__nv_bfloat16*>(stB.p);
-  int* eA = reinterpret_cast<int*>(exA.p);
-  int* eB = reinterpret_cast<int*>(exB.p);
-  oz_stage_kernel<<<blocks_for_rows((size_t)g.batch * rowsA), 256, 0, ex.stream>>>(g.A, g.am, g.ak, g.ab, g.M, g.K,
-                                                                                  g.batch, rowsA, k_pad, 0, fA, eA);
-  ex.count();
-  oz_stage_kernel<<<blocks_for_rows((size_t)g.batch * rowsB), 256, 0, ex.stream>>>(g.B, g.bn, g.bk, g.bb, g.N, g.K,
-                                                                                  g.batch, rowsB, k_pad, 1, fB, eB);
-  ex.count();
+  auto* eA = reinterpret_cast<unsigned*>(exA.p);
+  auto* eB = reinterpret_cast<unsigned*>(exB.p);
+  CC_CUDA(cudaMemsetAsync(eA, 0, (size_t)g.batch * rowsA * sizeof(unsigned), ex.stream));
+  CC_CUDA(cudaMemsetAsync(eB, 0, (size_t)g.batch * rowsB * sizeof(unsigned), ex.stream));
+  auto stage = [&](const double* src, const CIdx& rix, const CIdx& kix, const CIdx& bix, int rows, int rows_pad,
+                   int rev, unsigned* e, __nv_bfloat16* f) {
+    const size_t pieces1 = (size_t)g.batch * rows * ((g.K + ROW_PIECE - 1) / ROW_PIECE);
+    oz_rowexp_kernel<<<blocks_for_rows(pieces1), 256, 0, ex.stream>>>(src, rix, kix, bix, rows, g.K, g.batch,
+                                                                        rows_pad, e);
+    ex.count();
+    const size_t pieces2 = (size_t)g.batch * rows_pad * ((k_pad + ROW_PIECE - 1) / ROW_PIECE);
+    oz_digits_kernel<<<blocks_for_rows(pieces2), 256, 0, ex.stream>>>(src, rix, kix, bix, rows, g.K, g.batch,
+                                                                        rows_pad, k_pad, rev, e, f);
+    ex.count();
+  };
+  stage(g.A, g.am, g.ak, g.ab, g.M, rowsA, 0, eA, fA);
+  stage(g.B, g.bn, g.bk, g.bb, g.N, rowsB, 1, eB, fB);
   CC_CUDA(cudaGetLastError());
   CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM, true);
   CUtensorMap mB = make_map(fB, kk, rowsB, g.batch, TN, true);
@@ -939,7 +973,7 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
   const size_t items = rows * ((g.N + piece - 1) / piece);
   const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
-  oz_combine_kernel<<<rblocks, 256, 0, ex.stream>>>(g, a.part, nsplit, kseg, gsh, eA, rowsA, eB, rowsB, piece);
+  oz_combine_kernel<<<rblocks, 256, 0, ex.stream>>>(g, a.part, kseg, gsh, eA, rowsA, eB, rowsB, piece);
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);

@@ -45,8 +45,8 @@ CASES = {
     "o10v90n300_gap0.02_shift0.2": dict(sys=dict(o=10, v=90, naux=300, seed=5, gauge="haar", gap=0.02),
                                         shift=0.2, maxiter=150),
     # the near-degenerate workload itself (o=20 v=180 naux=600, gap 0.02 Eh)
-    "o20v180n600_gap0.02": dict(workload="o20v180_neardegenerate", shift=0.0, maxiter=60),
-    "o20v180n600_gap0.02_shift0.2": dict(workload="o20v180_neardegenerate", shift=0.2, maxiter=60),
+    "o20v180n600_gap0.02": dict(workload="o20v180_neardegenerate", shift=0.0, maxiter=40),
+    "o20v180n600_gap0.02_shift0.2": dict(workload="o20v180_neardegenerate", shift=0.2, maxiter=40),
 }
 for lam in (0.5, 0.6, 0.7, 0.8, 0.9):
     CASES[f"o10v90n900_rotated_lambda{lam}"] = dict(sys=dict(o=10, v=90, naux=900, seed=3, gauge="small"),
@@ -73,24 +73,31 @@ def run(name, spec):
         s = synth.make_system(**spec["sys"])
     B = s.B * spec.get("lam", 1.0)
     f, Bc, _ = cc.to_eigenbasis(s.fock, B, s.o)
-    energies = []
+    energies, hist = [], []
     t0 = time.time()
-    _, _, e, hist = cc.solve_fp_diis(f, Bc, s.o, tol=1e-8, maxiter=spec["maxiter"], shift=spec["shift"],
-                                     diis_size=8, diverge_at=1e3, energies=energies, verbose=True)
+    outcome = "not converged within the iteration cap"
+    e = None
+    for it, _, _, e, rn in cc.fp_diis_iterates(f, Bc, s.o, shift=spec["shift"], diis_size=8):
+        hist.append(rn)
+        energies.append(e)
+        print(f"  {name} it {it:3d}  |R| {rn:.3e}  E {e:.12f}", flush=True)
+        if rn < 1e-8:
+            outcome = "converged"
+            break
+        if not np.isfinite(rn) or rn > 1e3 * hist[0]:
+            outcome = "diverged"
+            break
+        if len(hist) >= spec["maxiter"]:
+            break
     rn = hist[-1]
-    if rn < 1e-8:
-        outcome = "converged"
-    elif not np.isfinite(rn) or rn > 1e3:
-        outcome = "diverged"
-    else:
-        outcome = "not converged within the iteration cap"
     return {"o": s.o, "v": s.v, "naux": s.naux, "lambda": spec.get("lam", 1.0), "shift": spec["shift"],
             "outcome": outcome, "iterations": len(hist), "final_res_norm": rn, "final_energy": e,
             "mp2_energy": energies[0] if energies else None, "min_res_norm": float(np.nanmin(hist)),
             "seconds": round(time.time() - t0, 1), "regime": regime(f, Bc, s.o),
             "res_norm_history": [float(f"{x:.3e}") for x in hist],
             "energy_history": [float(f"{x:.10f}") for x in energies],
-            "solver": "oracle fp+diis(8), eigenbasis, generalised MP2 start, stop at ||R|| > 1e3"}
+            "solver": "oracle fp+diis(8), eigenbasis, generalised MP2 start; diverged: ||R|| above 1e3 times "
+                      "its value at the start"}
 
 
 def main(names):
