@@ -331,45 +331,59 @@ def large_block(args, peaks, peak_kind):
     return out
 
 
-def served_block(args):
-    """The first --serve-default requests of the served mix, submitted at their Poisson arrival
-    times to the continuous-batching server, once on the mixed path and once on the FP64 path
-    (the same requests): p50/p99 time to solution, solves/s and convergence."""
+def serve_pass(reqs, prec, extra, args):
+    """Submits the requests at their arrival times to a fresh server and waits for all of them;
+    returns p50/p99 time to solution, solves/s and convergence."""
     import numpy as np
 
-    from paper_2608_06669_b300 import ccpnk, synth
+    from paper_2608_06669_b300 import ccpnk
+
+    srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=args.slots)
+    t_start = time.perf_counter()
+    tickets = []
+    for arrival, sy in reqs:
+        wait = arrival - (time.perf_counter() - t_start)
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append(srv.submit(sy.o, sy.v, sy.naux, sy.fock, sy.B, "pnk", prec, af_direct=1,
+                                  max_outer=args.max_newton, max_seconds=args.solve_seconds, **extra))
+    results = {}
+    while len(results) < len(tickets):
+        for t in tickets:
+            if t not in results:
+                r = srv.poll(t)
+                if r is not None:
+                    results[t] = r
+        time.sleep(0.002)
+    times = [srv.times(t) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([f - sub for sub, _, f in times])
+    span = max(f for _, _, f in times) - min(sub for sub, _, _ in times)
+    conv = [results[t][2]["status_code"] == 0 for t in tickets]
+    return {"requests": len(reqs), "solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(conv)), "makespan_s": span,
+            "max_concurrent": stats["max_running"],
+            "not_converged": [f"o{sy.o}v{sy.v}" for (_, sy), c in zip(reqs, conv) if not c]}
+
+
+def served_block(args):
+    """The first --serve-default requests of the served mix (Poisson arrivals, mean 20 ms),
+    each through the continuous-batching server: the mixed path (three-pass TF32 JVPs, FP64-
+    emulated outer residual) on all of them; the native FP64 path and the mixed path again on
+    the same subset of the requests with o <= --serve-fp64-max-o (native FP64 PNK of the larger
+    requests takes minutes: all 32 took 431 s on one B300); with --serve-fp64-all the native
+    FP64 path serves every request."""
+    from paper_2608_06669_b300 import synth
 
     reqs = synth.served_requests(args.serve_default)
-    out = {"requests": len(reqs), "slots": args.slots, "arrivals": "exponential, mean 20 ms"}
-    for key, prec, extra in (("mixed", "tf32x3", {"outer_prec": 5}), ("fp64", "fp64", {})):
-        srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=args.slots)
-        t_start = time.perf_counter()
-        tickets = []
-        for arrival, sy in reqs:
-            wait = arrival - (time.perf_counter() - t_start)
-            if wait > 0:
-                time.sleep(wait)
-            tickets.append(srv.submit(sy.o, sy.v, sy.naux, sy.fock, sy.B, "pnk", prec, af_direct=1,
-                                      max_outer=args.max_newton, max_seconds=args.solve_seconds, **extra))
-        results = {}
-        while len(results) < len(tickets):
-            for t in tickets:
-                if t not in results:
-                    r = srv.poll(t)
-                    if r is not None:
-                        results[t] = r
-            time.sleep(0.002)
-        times = [srv.times(t) for t in tickets]
-        stats = srv.stats()
-        srv.close()
-        lat = np.array([f - sub for sub, _, f in times])
-        span = max(f for _, _, f in times) - min(sub for sub, _, _ in times)
-        conv = [results[t][2]["status_code"] == 0 for t in tickets]
-        out[key] = {"solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
-                    "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(conv)), "makespan_s": span,
-                    "max_concurrent": stats["max_running"],
-                    "not_converged": [f"o{sy.o}v{sy.v}" for (_, sy), c in zip(reqs, conv) if not c],
-                    "outer_residual": "fp64emu" if key == "mixed" else "fp64"}
+    out = {"slots": args.slots, "arrivals": "exponential, mean 20 ms", "caps": {
+        "max_newton": args.max_newton, "max_seconds": args.solve_seconds}}
+    out["mixed"] = serve_pass(reqs, "tf32x3", {"outer_prec": 5}, args)
+    sub = reqs if args.serve_fp64_all else [(t, sy) for t, sy in reqs if sy.o <= args.serve_fp64_max_o]
+    out["subset"] = ("all" if args.serve_fp64_all else f"the {len(sub)} requests with o <= {args.serve_fp64_max_o}")
+    out["fp64_on_subset"] = serve_pass(sub, "fp64", {}, args)
+    out["mixed_on_subset"] = serve_pass(sub, "tf32x3", {"outer_prec": 5}, args)
     return out
 
 
@@ -726,6 +740,8 @@ def main():
     ap.add_argument("--large-newton", type=int, default=2, help="capped Newton steps at o=30 v=270")
     ap.add_argument("--fp64-large-jvp", action="store_true", help="also time one native FP64 JVP at o=30 v=270")
     ap.add_argument("--serve-default", type=int, default=32, help="requests of the served block (0: skip)")
+    ap.add_argument("--serve-fp64-max-o", type=int, default=8, help="native FP64 serves the requests with o <= this")
+    ap.add_argument("--serve-fp64-all", action="store_true", help="native FP64 serves every request of the block")
     ap.add_argument("--only-headline", action="store_true",
                     help="only the timed solves (the launch-list and profile captures run this)")
     ap.add_argument("--af-gmres", action="store_true", help="invert A_F by inner GMRES in the timed solves")

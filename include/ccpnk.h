@@ -128,9 +128,13 @@ const char* cc_last_error(const cc_ctx* ctx);
  * CC_OPT_WAIT_LIMIT_NS: bound, in nanoseconds of the GPU's global timer, on every wait of a
  *   device-side pipeline (default 4e9, at least 1e5); a wait that gives up makes the call
  *   return CC_ERR_TIMEOUT and leaves the context usable.
+ * CC_OPT_GRAPHS: 1 (default) replays the JVPs of an NK or PNK solve from CUDA graphs of the
+ *   tangent program (captured during the solve, released when it returns; the kernel timer, when
+ *   on, keeps them eager); 0 launches every kernel. Results are the same bits either way.
  * Returns CC_OK or CC_ERR_INVALID (unknown option, value out of range). */
 #define CC_OPT_STAGE_CACHE_BYTES 1
 #define CC_OPT_WAIT_LIMIT_NS 2
+#define CC_OPT_GRAPHS 3
 int cc_ctx_set_option(cc_ctx* ctx, int option, long long value);
 /* Self-test of the bounded device waits: runs one kernel whose wait on an mbarrier that nothing
  * arrives at gives up after CC_OPT_WAIT_LIMIT_NS, so the call returns CC_ERR_TIMEOUT; the

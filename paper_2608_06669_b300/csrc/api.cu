@@ -30,12 +30,13 @@ void* Pool::get(size_t bytes) {
   int best = -1;
   for (size_t i = 0; i < blocks_.size(); ++i) {
     const Block& b = blocks_[i];
-    if (!b.used && b.bytes >= bytes && b.bytes <= 2 * bytes + 4096 &&
+    if (!b.used && !b.pins && b.bytes >= bytes && b.bytes <= 2 * bytes + 4096 &&
         (best < 0 || b.bytes < blocks_[best].bytes))
       best = (int)i;
   }
   if (best >= 0) {
     blocks_[best].used = true;
+    if (record) record->push_back(blocks_[best].p);
     return blocks_[best].p;
   }
   if (budget_ && held_ + bytes > budget_) release_free();
@@ -53,9 +54,20 @@ void* Pool::get(size_t bytes) {
       fail(CC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
   }
-  blocks_.push_back({p, bytes, true});
+  blocks_.push_back({p, bytes, true, 0});
   held_ += bytes;
+  if (record) record->push_back(p);
   return p;
+}
+
+void Pool::pin(void* p) {
+  for (auto& b : blocks_)
+    if (b.p == p) b.pins += 1;
+}
+
+void Pool::unpin(void* p) {
+  for (auto& b : blocks_)
+    if (b.p == p && b.pins > 0) b.pins -= 1;
 }
 
 void Pool::put(void* p) {
@@ -111,7 +123,7 @@ void Prof::reset() {
 void Pool::release_free() {
   std::vector<Block> keep;
   for (auto& b : blocks_) {
-    if (b.used) keep.push_back(b);
+    if (b.used || b.pins) keep.push_back(b);
     else {
       cudaFree(b.p);
       held_ -= b.bytes;
@@ -283,6 +295,9 @@ int cc_ctx_set_option(cc_ctx* ctx, int option, long long value) {
     } else if (option == CC_OPT_WAIT_LIMIT_NS) {
       CC_REQUIRE(value >= 100000, CC_ERR_INVALID, "CC_OPT_WAIT_LIMIT_NS: at least 1e5 ns");
       ctx->wait_ns = (unsigned long long)value;
+    } else if (option == CC_OPT_GRAPHS) {
+      CC_REQUIRE(value == 0 || value == 1, CC_ERR_INVALID, "CC_OPT_GRAPHS: 0 or 1");
+      ctx->graphs = (int)value;
     } else {
       fail(CC_ERR_INVALID, "unknown option");
     }

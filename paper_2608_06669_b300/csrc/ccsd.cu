@@ -385,7 +385,10 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
 
 void Engine::value(const double* t, double* r, double* energy_dev, cc_precision prec) {
   const int o = s_.o, v = s_.v, n = s_.n;
-  stage_.clear();  // the values change: staged copies of the old ones are stale
+  // the values change: staged copies of the old ones are stale (kept in place for the graphs)
+  if (graphs_on_) stage_.mark_stale();
+  else stage_.clear();
+  first_since_value_ = true;
   if (t != t_.val.p) k_copy(ex_, s_.namp(), t, t_.val.p);
   program(false, prec, r);
   if (energy_dev)
@@ -394,7 +397,88 @@ void Engine::value(const double* t, double* r, double* energy_dev, cc_precision 
 
 void Engine::tangent(const double* d, double* jd, cc_precision prec) {
   if (d != t_.tan.p) k_copy(ex_, s_.namp(), d, t_.tan.p);
-  program(true, prec, jd);
+  const bool graph = graphs_on_ && prec == graph_prec_ && !(ex_.prof && ex_.prof->on);
+  TanGraph& G = graphs_[first_since_value_ ? 0 : 1];
+  first_since_value_ = false;
+  if (!graph) {
+    program(true, prec, jd);
+    return;
+  }
+  if (!G.exec) {
+    if (G.eager < 1) {
+      ++G.eager;
+      program(true, prec, jd);
+      return;
+    }
+    capture(G, prec);
+  }
+  CC_CUDA(cudaGraphLaunch(G.exec, ex_.stream));
+  ex_.count(G.launches);
+  k_copy(ex_, s_.namp(), jout_.p, jd);
+}
+
+void Engine::capture(TanGraph& G, cc_precision prec) {
+  if (!cap_stream_) CC_CUDA(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+  const Exec saved = ex_;
+  uint64_t nodes = 0;
+  std::vector<void*> rec;
+  ex_.stream = cap_stream_;  // captured on a private stream, launched on the context's
+  ex_.launches = &nodes;
+  ex_.pool->record = &rec;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    try {
+      program(true, prec, jout_.p);
+    } catch (...) {
+      cudaStreamEndCapture(cap_stream_, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      ex_ = saved;
+      ex_.pool->record = nullptr;
+      throw;
+    }
+    e = cudaStreamEndCapture(cap_stream_, &graph);
+  }
+  ex_ = saved;
+  ex_.pool->record = nullptr;
+  CC_CUDA(e);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CC_CUDA(e);
+  std::sort(rec.begin(), rec.end());
+  rec.erase(std::unique(rec.begin(), rec.end()), rec.end());
+  for (void* p : rec) ex_.pool->pin(p);
+  G.pinned = std::move(rec);
+  G.exec = exec;
+  G.launches = nodes;
+}
+
+void Engine::begin_graphs(cc_precision prec) {
+  end_graphs();
+  if (!jout_.p) jout_.alloc(ex_.pool, s_.namp());
+  graphs_on_ = true;
+  graph_prec_ = prec;
+  first_since_value_ = true;
+}
+
+void Engine::end_graphs() noexcept {
+  if (!graphs_on_) return;
+  cudaStreamSynchronize(ex_.stream);  // no replay may still be running when its scratch is released
+  for (auto& G : graphs_) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    for (void* p : G.pinned) ex_.pool->unpin(p);
+    G = TanGraph{};
+  }
+  graphs_on_ = false;
+  stage_.clear();
+  cudaGetLastError();
+}
+
+Engine::~Engine() {
+  end_graphs();
+  if (cap_stream_) cudaStreamDestroy(cap_stream_);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,6 +36,7 @@ size_t stage_cache_cap(int o, int v, int P);
 class Engine {
  public:
   Engine(const Exec& ex, const System& s);
+  ~Engine();
   // R(t), E(t): t = [t1 | t2] on the device (namp doubles), r = [r1 | r2].
   // Leaves the intermediates of t in place for later tangent() calls.
   void value(const double* t, double* r, double* energy_dev, cc_precision prec);
@@ -45,6 +46,14 @@ class Engine {
   // Takes the context's current settings (wait limit, staged-operand cache size); a smaller
   // cache drops what it kept.
   void rebind(const Exec& ex);
+  // CUDA graphs for the JVPs of one solve: between begin_graphs and end_graphs, the tangent
+  // program at prec is captured once as it runs right after a residual evaluation (when it
+  // re-stages the value-side operands it keeps) and once as it runs later (when it reuses them),
+  // and every further JVP replays the matching graph. The graphs read and write the engine's
+  // own buffers at fixed addresses; their scratch blocks stay pinned in the pool until
+  // end_graphs. Profiled runs (the kernel timer on) stay eager.
+  void begin_graphs(cc_precision prec);
+  void end_graphs() noexcept;
   double* scratch() { return scratch_.p; }
   size_t scratch_count() const { return scratch_.n; }
 
@@ -68,6 +77,18 @@ class Engine {
   int w2_mode_ = -1;      // precision whose layout W2_ holds
   StageCache stage_;      // staged value-side operands of the tangent program (cleared by value())
   DBuf<double> scratch_;  // reduction partials
+  struct TanGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> pinned;  // pool blocks the captured kernels use as scratch
+    uint64_t launches = 0;      // kernel nodes (counted as launches at every replay)
+    int eager = 0;              // eager runs before the capture (they warm the pool and the cache)
+  };
+  void capture(TanGraph& G, cc_precision prec);
+  TanGraph graphs_[2];          // [0]: first JVP after a residual evaluation, [1]: the others
+  bool graphs_on_ = false, first_since_value_ = true;
+  cc_precision graph_prec_ = CC_FP64;
+  cudaStream_t cap_stream_ = nullptr;
+  DBuf<double> jout_;           // the captured program's output
 };
 
 // Readies cc_energy_noalloc on the current device for this problem: loads its module, looks up

@@ -40,12 +40,19 @@ class Pool {
   void release_free();  // frees cached blocks
   size_t held() const { return held_; }
   size_t budget() const { return budget_; }
+  // CUDA-graph support: while record is set, every block handed out is appended to it; a pinned
+  // block is never handed out again (nor freed) until it is unpinned, so a captured graph keeps
+  // exclusive use of the scratch blocks its kernels were recorded with.
+  std::vector<void*>* record = nullptr;
+  void pin(void* p);
+  void unpin(void* p);
 
  private:
   struct Block {
     void* p;
     size_t bytes;
     bool used;
+    int pins = 0;
   };
   std::vector<Block> blocks_;
   size_t budget_;
@@ -117,6 +124,7 @@ struct Exec {
   Prof* prof = nullptr;
   unsigned long long wait_ns = 4000000000ull;  // bound on every device-side wait (global timer)
   long long stage_cap = -1;                    // bytes of kept staged operands (-1: the default)
+  int graphs = 1;                              // replay the JVPs of a solve from CUDA graphs
   void count(uint64_t k = 1) const {
     if (launches) *launches += k;
   }
@@ -199,12 +207,18 @@ struct StageCache {
   struct Ent {
     StageKey key;
     DBuf<double> buf;
+    bool fresh = true;  // false: the source changed since the copy was staged (re-stage in place)
   };
   std::vector<Ent> ents;
   size_t bytes = 0, cap = 0;
   void clear() {
     ents.clear();
     bytes = 0;
+  }
+  // keeps the buffers (and so their addresses, which a captured graph may hold) but marks every
+  // copy out of date
+  void mark_stale() {
+    for (auto& e : ents) e.fresh = false;
   }
 };
 

@@ -733,8 +733,13 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
     if (g.cache && (g.cache_mask & which)) {
       const StageKey key{src, rix, kix, bix, rows, g.K, g.batch, rows_pad, k_pad, nseg, seg_lo, BF ? 1 : 0};
       for (auto& e : g.cache->ents)
-        if (e.key == key) return reinterpret_cast<T*>(e.buf.p);
-      if (g.cache->bytes + dbl * 8 <= g.cache->cap) {
+        if (e.key == key) {
+          if (e.fresh) return reinterpret_cast<T*>(e.buf.p);
+          dst = e.buf.p;  // out of date: staged again in place (same address)
+          e.fresh = true;
+          break;
+        }
+      if (!dst && g.cache->bytes + dbl * 8 <= g.cache->cap) {
         // allocate first: if the pool throws, no entry is left keyed to a missing buffer
         DBuf<double> buf(ex.pool, dbl);
         g.cache->ents.emplace_back();

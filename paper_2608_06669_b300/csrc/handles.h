@@ -18,6 +18,7 @@ struct cc_ctx {
   ccpnk::Prof prof;
   unsigned long long wait_ns = 4000000000ull;  // CC_OPT_WAIT_LIMIT_NS
   long long stage_cap = -1;                    // CC_OPT_STAGE_CACHE_BYTES (-1: the default)
+  int graphs = 1;                              // CC_OPT_GRAPHS
   ccpnk::Exec ex() {
     ccpnk::Exec e;
     e.stream = stream;
@@ -28,6 +29,7 @@ struct cc_ctx {
     e.prof = &prof;
     e.wait_ns = wait_ns;
     e.stage_cap = stage_cap;
+    e.graphs = graphs;
     return e;
   }
 };

@@ -315,6 +315,13 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     k_fill(ex, n1, 0.0, t);
   }
 
+  // the JVPs of the Newton family replay CUDA graphs of the tangent program (released on return)
+  struct GraphWindow {
+    Engine& e;
+    ~GraphWindow() { e.end_graphs(); }
+  } window{eng};
+  if (ex.graphs && !opt.jvp_fd && (opt.method == CC_NK || opt.method == CC_PNK)) eng.begin_graphs(opt.prec);
+
   double energy = 0.0, rn = 0.0, rn_prev = 0.0, eta_prev = opt.eta_max;
   int status = CC_ERR_NOT_CONVERGED;
   // no point asking the linear solve for more than its operator's precision delivers

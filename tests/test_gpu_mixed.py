@@ -204,3 +204,25 @@ def test_mixed_jvp_error_table(ctx):
         with open(os.path.join(out, "jvp_error_table.json"), "w") as fh:
             json.dump({"workload": "o10v90_rotated, MP2 start, random direction (scale 0.01)",
                        "normwise_error_vs_oracle": table}, fh, indent=1)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp64"])
+def test_graph_replayed_jvps_give_the_same_solve(ctx, prec):
+    """The JVPs of a PNK solve replayed from CUDA graphs of the tangent program (the default)
+    give the same solve, bit for bit, as launching every kernel."""
+    s = synth.workload("o10v90_rotated" if prec == "tf32x3" else "o5v20_canonical")
+    g = gsys(ctx, s)
+    runs = {}
+    for graphs in (1, 0):
+        ctx.set_option("graphs", graphs)
+        n0 = ctx.launches
+        t1, t2, rep = g.solve("pnk", prec, af_direct=1, outer_prec=5 if prec == "tf32x3" else 0)
+        runs[graphs] = (t1, t2, rep, ctx.launches - n0)
+    ctx.set_option("graphs", 1)
+    (a1, a2, ra, na), (b1, b2, rb, nb) = runs[1], runs[0]
+    assert ra["status_code"] == 0 == rb["status_code"]
+    for k in ("newton_iters", "jvps", "krylov_iters", "residual_evals"):
+        assert ra[k] == rb[k], k
+    assert ra["energy"] == rb["energy"] and np.array_equal(a2, b2) and np.array_equal(a1, b1)
+    # a replay counts its kernel nodes; the replays add one output copy each
+    assert nb <= na <= nb + ra["jvps"]
