@@ -331,14 +331,17 @@ def large_block(args, peaks, peak_kind):
     return out
 
 
-def serve_pass(reqs, prec, extra, args):
+def serve_pass(reqs, prec, extra, args, slots=None, group=1):
     """Submits the requests at their arrival times to a fresh server and waits for all of them;
-    returns p50/p99 time to solution, solves/s and convergence."""
+    returns p50/p99 time to solution, solves/s and convergence. group > 1: grouped mode (a slot
+    solves up to that many compatible requests together, in lockstep)."""
     import numpy as np
 
     from paper_2608_06669_b300 import ccpnk
 
-    srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=args.slots)
+    srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=slots or args.slots)
+    if group > 1:
+        srv.set_grouping(group)
     t_start = time.perf_counter()
     tickets = []
     for arrival, sy in reqs:
@@ -361,7 +364,8 @@ def serve_pass(reqs, prec, extra, args):
     lat = np.array([f - sub for sub, _, f in times])
     span = max(f for _, _, f in times) - min(sub for sub, _, _ in times)
     conv = [results[t][2]["status_code"] == 0 for t in tickets]
-    return {"requests": len(reqs), "solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
+    return {"requests": len(reqs), "slots": slots or args.slots, "group": group,
+            "solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(conv)), "makespan_s": span,
             "max_concurrent": stats["max_running"],
             "not_converged": [f"o{sy.o}v{sy.v}" for (_, sy), c in zip(reqs, conv) if not c]}
@@ -373,13 +377,17 @@ def served_block(args):
     emulated outer residual) on all of them; the native FP64 path and the mixed path again on
     the same subset of the requests with o <= --serve-fp64-max-o (native FP64 PNK of the larger
     requests takes minutes: all 32 took 431 s on one B300); with --serve-fp64-all the native
-    FP64 path serves every request."""
+    FP64 path serves every request. The mixed path also runs in the server's grouped mode
+    (--group-slots slots, each solving up to --serve-group requests in one lockstep batch)."""
     from paper_2608_06669_b300 import synth
 
     reqs = synth.served_requests(args.serve_default)
     out = {"slots": args.slots, "arrivals": "exponential, mean 20 ms", "caps": {
         "max_newton": args.max_newton, "max_seconds": args.solve_seconds}}
     out["mixed"] = serve_pass(reqs, "tf32x3", {"outer_prec": 5}, args)
+    # grouped mode: fewer slots, each solving up to --serve-group requests in one lockstep batch
+    out["mixed_grouped"] = serve_pass(reqs, "tf32x3", {"outer_prec": 5}, args, slots=args.group_slots,
+                                      group=args.serve_group)
     sub = reqs if args.serve_fp64_all else [(t, sy) for t, sy in reqs if sy.o <= args.serve_fp64_max_o]
     out["subset"] = ("all" if args.serve_fp64_all else f"the {len(sub)} requests with o <= {args.serve_fp64_max_o}")
     out["fp64_on_subset"] = serve_pass(sub, "fp64", {}, args)
@@ -800,6 +808,8 @@ def main():
     ap.add_argument("--serve-default", type=int, default=32, help="requests of the served block (0: skip)")
     ap.add_argument("--serve-fp64-max-o", type=int, default=8, help="native FP64 serves the requests with o <= this")
     ap.add_argument("--serve-fp64-all", action="store_true", help="native FP64 serves every request of the block")
+    ap.add_argument("--serve-group", type=int, default=8, help="requests per lockstep batch in the grouped pass")
+    ap.add_argument("--group-slots", type=int, default=2, help="slots of the grouped pass")
     ap.add_argument("--only-headline", action="store_true",
                     help="only the timed solves (the launch-list and profile captures run this)")
     ap.add_argument("--af-gmres", action="store_true", help="invert A_F by inner GMRES in the timed solves")

@@ -215,6 +215,19 @@ int cc_apply_AF(cc_ctx* ctx, cc_sys* sys, const double* x1, const double* x2,
 int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2,
              int use_guess, cc_report* report);
 
+/* Solves nsys problems of one context together (the batching of the serving pattern; the paper
+ * solves one problem at a time). NK and PNK run in lockstep: every residual and JVP is evaluated
+ * for all unfinished problems at once, the same contraction of every problem in one group, whose
+ * tensor-core contractions share persistent grouped launches (up to 16 problems per launch), and
+ * the Krylov iterations of each Newton step advance together until each problem's forcing
+ * condition holds. Each problem's arithmetic is that of cc_solve from the generalised MP2 start,
+ * so its result is the same (bit for bit). Other methods solve the problems one after the other.
+ * sys: nsys distinct problems of ctx; t1s / t2s: nsys output pointers each (host or device; the
+ * arrays may be NULL), written as each problem finishes; reports: nsys entries. Returns CC_OK
+ * once all have finished (each problem's own status is in its report), or an error of the call. */
+int cc_solve_batch(cc_ctx* ctx, int nsys, cc_sys* const* sys, const cc_solve_opts* opts, double* const* t1s,
+                   double* const* t2s, cc_report* reports);
+
 /* The correlation energy E(t) of cc_residual, computed without allocating any device memory.
  * The paper has no counterpart: this is a service for callers that cannot call cudaMalloc at
  * this point (code inside another framework's memory arena, real-time loops that must stay
@@ -238,6 +251,12 @@ int cc_energy_noalloc(const cc_sys* sys, const double* t1, const double* t2, dou
  * device-memory estimate fits under mem_budget (0: no budget), so the kernels of different
  * requests overlap on the device. Results are bitwise independent of what else runs. */
 int cc_server_create(cc_server** srv, int device, size_t mem_budget, int max_slots);
+/* Grouped mode: with group_max > 1 a slot that takes a waiting request also takes up to
+ * group_max - 1 later waiting requests with identical NK/PNK options whose memory estimates fit,
+ * and solves them as one lockstep batch (cc_solve_batch: the same contraction of every request in
+ * one grouped launch); each request is posted as soon as it has finished, with the result it
+ * would have alone. 1 (the default) solves one request per slot. CC_ERR_INVALID outside 1..64. */
+int cc_server_set_grouping(cc_server* srv, int group_max);
 /* Finishes the running solves, drops queued ones and frees everything. */
 void cc_server_destroy(cc_server* srv);
 /* Copies the problem (host pointers) before returning; ticket identifies the request.

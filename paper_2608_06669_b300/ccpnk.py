@@ -83,12 +83,15 @@ def lib() -> ctypes.CDLL:
             "cc_jvp_multi": (i, [vp, vp, vp, vp, i, vp, vp, vp, vp, i]),
             "cc_apply_AF": (i, [vp, vp, vp, vp, vp, vp, i, i]),
             "cc_solve": (i, [vp, vp, ctypes.POINTER(SolveOpts), vp, vp, i, ctypes.POINTER(Report)]),
+            "cc_solve_batch": (i, [vp, i, ctypes.POINTER(vp), ctypes.POINTER(SolveOpts), ctypes.POINTER(vp),
+                                   ctypes.POINTER(vp), ctypes.POINTER(Report)]),
             "cc_energy_noalloc": (i, [vp, vp, vp, vp, vp]),
             "cc_server_create": (i, [pp, i, sz, i]),
             "cc_server_destroy": (None, [vp]),
             "cc_serve_submit": (i, [vp, i, i, i, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(u64)]),
             "cc_serve_poll": (i, [vp, u64, ctypes.POINTER(Report), vp, vp]),
             "cc_serve_cancel": (i, [vp, u64]),
+            "cc_server_set_grouping": (i, [vp, i]),
             "cc_serve_times": (i, [vp, u64, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
             "cc_server_stats": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)]),
         }
@@ -307,6 +310,25 @@ class System:
         return o1, o2, d
 
 
+def solve_batch(ctx: Context, systems, method="pnk", prec="fp64", **kw):
+    """cc_solve_batch: solves the systems (of one context) together in lockstep; returns a list
+    of (t1, t2, report dict) in the systems' order, amplitudes as numpy arrays."""
+    n = len(systems)
+    opts = default_opts(method, prec, **kw)
+    outs = [(np.empty((s.o, s.v)), np.empty((s.o, s.o, s.v, s.v))) for s in systems]
+    hs = (ctypes.c_void_p * n)(*[s.h for s in systems])
+    p1 = (ctypes.c_void_p * n)(*[o[0].ctypes.data for o in outs])
+    p2 = (ctypes.c_void_p * n)(*[o[1].ctypes.data for o in outs])
+    reps = (Report * n)()
+    _check(ctx.h, lib().cc_solve_batch(ctx.h, n, hs, ctypes.byref(opts), p1, p2, reps))
+    res = []
+    for k in range(n):
+        d = reps[k].as_dict()
+        d["status_code"] = d["status"]
+        res.append((outs[k][0], outs[k][1], d))
+    return res
+
+
 class Server:
     """The continuous-batching server (cc_server): submit() returns a ticket at once; poll()
     returns None while the request waits or runs, then (t1, t2, report dict)."""
@@ -342,6 +364,12 @@ class Server:
         d = rep.as_dict()
         d["status_code"] = st
         return t1, t2, d
+
+    def set_grouping(self, group_max: int):
+        """cc_server_set_grouping: a slot solves up to group_max compatible requests together."""
+        st = lib().cc_server_set_grouping(self.h, int(group_max))
+        if st < 0:
+            raise CCError(st, "cc_server_set_grouping failed")
 
     def cancel(self, ticket: int) -> int:
         """cc_serve_cancel: drops a waiting request or stops a running one."""

@@ -498,9 +498,52 @@ int cc_solve(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, do
   return ccpnk::solve_cancellable(ctx, sys, opts, t1, t2, use_guess, report, nullptr);
 }
 
+int cc_solve_batch(cc_ctx* ctx, int nsys, cc_sys* const* sys, const cc_solve_opts* opts, double* const* t1s,
+                   double* const* t2s, cc_report* reports) {
+  return ccpnk::solve_batch_notify(ctx, nsys, sys, opts, t1s, t2s, reports, nullptr, nullptr);
+}
+
 }  // extern "C"
 
 namespace ccpnk {
+
+int solve_batch_notify(cc_ctx* ctx, int nsys, cc_sys* const* sys, const cc_solve_opts* opts, double* const* t1s,
+                       double* const* t2s, cc_report* reports, const std::function<void(int, int)>& notify,
+                       const std::vector<const std::atomic<int>*>* cancel) {
+  if (!ctx || !sys || !opts || nsys < 0 || (nsys > 0 && !reports)) return CC_ERR_INVALID;
+  return guarded(ctx, [&]() {
+    check_prec(opts->prec);
+    CC_REQUIRE(opts->method >= CC_FP_DIIS && opts->method <= CC_INK, CC_ERR_INVALID, "unknown method");
+    if (nsys == 0) return CC_OK;
+    Exec ex = ctx->ex();
+    std::vector<System*> ss;
+    std::vector<Engine*> es;
+    std::vector<DBuf<double>> tb(nsys);
+    std::vector<double*> ts;
+    for (int k = 0; k < nsys; ++k) {
+      CC_REQUIRE(sys[k] && sys[k]->ctx == ctx, CC_ERR_INVALID, "every problem must belong to the context");
+      for (int j = 0; j < k; ++j) CC_REQUIRE(sys[j] != sys[k], CC_ERR_INVALID, "a problem appears twice");
+      ss.push_back(&sys[k]->s);
+      es.push_back(&engine(sys[k]));
+      tb[k].alloc(ex.pool, sys[k]->s.namp());
+      ts.push_back(tb[k].p);
+    }
+    std::vector<cc_report> reps;
+    // each problem's amplitudes and report are handed out as soon as it has finished
+    auto done = [&](int k, int st) {
+      const System& s = *ss[k];
+      const size_t ov = (size_t)s.o * s.v;
+      if (t1s) copy_out(ctx, t1s[k], ts[k], ov);
+      if (t2s) copy_out(ctx, t2s[k], ts[k] + ov, s.namp() - ov);
+      CC_CUDA(cudaStreamSynchronize(ctx->stream));
+      reports[k] = reps[k];
+      if (notify) notify(k, st);
+    };
+    solve_batch(ex, ss, es, *opts, ts, reps, done, cancel);
+    CC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CC_OK;
+  });
+}
 
 int solve_cancellable(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2, int use_guess,
                       cc_report* report, const std::atomic<int>* cancel) {

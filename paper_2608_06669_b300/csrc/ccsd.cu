@@ -15,6 +15,7 @@
 // (App. B, Eq. AnalyticJVP) and the values of A and B are those kept from the residual at t.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 
 #include "ccsd.h"
 
@@ -218,7 +219,30 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
 void Engine::program(bool tan, cc_precision prec, double* rout) {
   const int o = s_.o, v = s_.v, n = s_.n, P = s_.P;
   const size_t ov = (size_t)o * v, oovv = (size_t)o * o * v * v;
-  const Exec& ex = ex_;
+  // Every launch of the program goes through run (kernels) or con (contractions): executed at
+  // once, or, while rec_ is set, recorded for a lockstep run over several engines. A recorded
+  // kernel closure holds the pointers it needs by value.
+  auto run = [&](std::function<void(const Exec&)> f) {
+    if (rec_) rec_->push_back(Op{Op::KERNEL, ContractSpec{}, std::move(f)});
+    else f(ex_);
+  };
+  auto con = [&](double alpha, const TView& A, const TView& B, double beta, const TView& C, int mask) {
+    StageCache* cache = mask ? &stage_ : nullptr;
+    if (rec_) {
+      Op op;
+      op.kind = Op::CONTRACT;
+      op.c.alpha = alpha;
+      op.c.beta = beta;
+      op.c.A = A;
+      op.c.B = B;
+      op.c.C = C;
+      op.c.cache = cache;
+      op.c.cache_mask = mask;
+      rec_->push_back(std::move(op));
+    } else {
+      contract(ex_, prec, alpha, A, B, beta, C, nullptr, nullptr, nullptr, cache, mask);
+    }
+  };
 
   auto dyn = [&](Pair& x, size_t off, const char* lab, std::initializer_list<int> ext) {
     TP r;
@@ -260,16 +284,16 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
   // until the next value() call, so its tensor-core staging may be kept across JVPs.
   auto bil = [&](double alpha, const TP& A, const TP& B, double beta, const TP& C) {
     if (!tan) {
-      contract(ex, prec, alpha, A.v, B.v, beta, C.v);
+      con(alpha, A.v, B.v, beta, C.v, 0);
       return;
     }
     double b = beta;
     if (A.dyn) {
-      contract(ex, prec, alpha, A.t, B.v, b, C.t, nullptr, nullptr, nullptr, &stage_, 2);
+      con(alpha, A.t, B.v, b, C.t, 2);
       b = 1.0;
     }
     if (B.dyn) {
-      contract(ex, prec, alpha, A.v, B.t, b, C.t, nullptr, nullptr, nullptr, &stage_, 1);
+      con(alpha, A.v, B.t, b, C.t, 1);
       b = 1.0;
     }
   };
@@ -287,26 +311,53 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
   (void)T1;
 
   // amplitudes u = 2 t - t(i<->j)
-  k_make_u(ex, o, v, cur(t_) + ov, cur(u_));
+  {
+    double *tt = cur(t_) + ov, *uu = cur(u_);
+    run([=](const Exec& e) { k_make_u(e, o, v, tt, uu); });
+  }
 
   // ---- a1: T1 dressing of the DF factor -------------------------------------------------
   // Bt_oo = B_oo + B_ov t1^T
-  if (!tan) k_copy(ex, (size_t)P * o * o, s_.Boo.p, Btoo_.val.p);
+  if (!tan) {
+    const double* src = s_.Boo.p;
+    double* dst = Btoo_.val.p;
+    run([=](const Exec& e) { k_copy(e, (size_t)P * o * o, src, dst); });
+  }
   bil(1.0, Bov("Pic"), t1l("jc"), tan ? 0.0 : 1.0, Boo("Pij"));
   // Bt_vv = B_vv - t1^T B_ov
-  if (!tan) k_copy(ex, (size_t)P * v * v, s_.Bvv.p, Btvv_.val.p);
+  if (!tan) {
+    const double* src = s_.Bvv.p;
+    double* dst = Btvv_.val.p;
+    run([=](const Exec& e) { k_copy(e, (size_t)P * v * v, src, dst); });
+  }
   bil(-1.0, t1l("ka"), Bov("Pkb"), tan ? 0.0 : 1.0, Bvv("Pab"));
   // Bt_vo = B_vo + B_vv t1^T - t1^T Bt_oo
-  if (!tan) k_transpose(ex, P, o, v, s_.Bov.p, (long long)o * v, v, Btvo_.val.p, (long long)v * o, o);
+  if (!tan) {
+    const double* src = s_.Bov.p;
+    double* dst = Btvo_.val.p;
+    run([=](const Exec& e) { k_transpose(e, P, o, v, src, (long long)o * v, v, dst, (long long)v * o, o); });
+  }
   bil(1.0, cst(s_.Bvv.p, "Pac", {P, v, v}), t1l("ic"), tan ? 0.0 : 1.0, Bvo("Pai"));
   bil(-1.0, t1l("ka"), Boo("Pki"), 1.0, Bvo("Pai"));
-  k_trace_batched(ex, P, o, cur(Btoo_), cur(gam_));
+  {
+    double *bo = cur(Btoo_), *gm = cur(gam_);
+    run([=](const Exec& e) { k_trace_batched(e, P, o, bo, gm); });
+  }
 
   // ---- dressed Fock matrix Ft = X h Y + 2 sum_P Bt gamma - sum_Pk Bt_pk Bt_kq -----------
-  if (!tan) k_copy(ex, (size_t)n * n, s_.h.p, hY_.val.p);
-  else k_fill(ex, (size_t)n * n, 0.0, hY_.tan.p);
+  if (!tan) {
+    const double* src = s_.h.p;
+    double* dst = hY_.val.p;
+    run([=](const Exec& e) { k_copy(e, (size_t)n * n, src, dst); });
+  } else {
+    double* dst = hY_.tan.p;
+    run([=](const Exec& e) { k_fill(e, (size_t)n * n, 0.0, dst); });
+  }
   bil(1.0, csts(s_.h.p + o, "pc", {n, v}, {n, 1}), t1l("jc"), 1.0, dyns(hY_, 0, "pj", {n, o}, {n, 1}));
-  k_copy(ex, (size_t)n * n, cur(hY_), cur(Ft_));
+  {
+    double *src = cur(hY_), *dst = cur(Ft_);
+    run([=](const Exec& e) { k_copy(e, (size_t)n * n, src, dst); });
+  }
   bil(-1.0, t1l("ka"), dyns(hY_, 0, "kq", {o, n}, {n, 1}), 1.0, dyns(Ft_, (size_t)o * n, "aq", {v, n}, {n, 1}));
   TP Foo = dyns(Ft_, 0, "ij", {o, o}, {n, 1});
   TP Fov = dyns(Ft_, o, "kc", {o, v}, {n, 1});
@@ -324,7 +375,10 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
 
   // ---- singles residual -----------------------------------------------------------------
   TP R1 = out(0, "ia", {o, v});
-  k_transpose(ex, 1, v, o, cur(Ft_) + (size_t)o * n, 0, n, rout, 0, v);  // Ft_vo^T
+  {
+    double* src = cur(Ft_) + (size_t)o * n;
+    run([=](const Exec& e) { k_transpose(e, 1, v, o, src, 0, n, rout, 0, v); });  // Ft_vo^T
+  }
   bil(1.0, Bov("Pkc"), ul("kicd"), 0.0, dyn(Z_, 0, "Pid", {P, o, v}));
   bil(1.0, dyn(Z_, 0, "Pid", {P, o, v}), Bvv("Pad"), 1.0, R1);
   bil(1.0, Bov("Plc"), ul("klac"), 0.0, dyn(Wk_, 0, "Pka", {P, o, v}));
@@ -337,20 +391,23 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
   // (ai|bj)~
   bil(1.0, Bvo("Pai"), Bvo("Pbj"), 0.0, R2);
   // particle-particle ladder sum_cd (ac|bd)~ t_ij^cd
+  // (the ladder runs as one step of its own engine in a lockstep run; its GEMMs are large)
   if (!tan) {
-    ladder(Btvv_.val.p, Btvv_.val.p, P, t_.val.p + ov, r2, prec);
+    run([=](const Exec&) { ladder(Btvv_.val.p, Btvv_.val.p, P, t_.val.p + ov, r2, prec); });
   } else {
     // d[(ac|bd)~ t] = (ac|bd)~ dt + sum_P (dBt_ac Bt_bd + Bt_ac dBt_bd) t; the second factor
     // pair, stacked along the auxiliary index, is again symmetric under (a,c) <-> (b,d)
-    ladder(Btvv_.val.p, Btvv_.val.p, P, t_.tan.p + ov, r2, prec, true, false);
-    const size_t pvv = (size_t)P * v * v;
-    double* Xs = XsYs_.p;
-    double* Ys = XsYs_.p + 2 * pvv;
-    k_copy(ex, pvv, Btvv_.tan.p, Xs);
-    k_copy(ex, pvv, Btvv_.val.p, Xs + pvv);
-    k_copy(ex, pvv, Btvv_.val.p, Ys);
-    k_copy(ex, pvv, Btvv_.tan.p, Ys + pvv);
-    ladder(Xs, Ys, 2 * P, t_.val.p + ov, r2, prec, false, true);
+    run([=](const Exec& e) {
+      ladder(Btvv_.val.p, Btvv_.val.p, P, t_.tan.p + ov, r2, prec, true, false);
+      const size_t pvv = (size_t)P * v * v;
+      double* Xs = XsYs_.p;
+      double* Ys = XsYs_.p + 2 * pvv;
+      k_copy(e, pvv, Btvv_.tan.p, Xs);
+      k_copy(e, pvv, Btvv_.val.p, Xs + pvv);
+      k_copy(e, pvv, Btvv_.val.p, Ys);
+      k_copy(e, pvv, Btvv_.tan.p, Ys + pvv);
+      ladder(Xs, Ys, 2 * P, t_.val.p + ov, r2, prec, false, true);
+    });
   }
   // hole ladder with its quadratic part: W_klij = (ki|lj)~ + sum_cd (kc|ld) t_ij^cd
   TP Woo = dyn(Woo_, 0, "klij", {o, o, o, o});
@@ -371,14 +428,23 @@ void Engine::program(bool tan, cc_precision prec, double* rout) {
   bil(0.5, ul("ilad"), cst(s_.Lovov.p, "ldkc", {o, v, o, v}), 1.0, Dl("kcia"));
   bil(0.5, Dl("kcia"), ul("jkbc"), 1.0, X);
   // Fock-like intermediates
-  k_copy3d(ex, 1, v, v, cur(Ft_) + (size_t)o * n + o, 0, n, cur(Gv_), 0, v);
+  {
+    double *src = cur(Ft_) + (size_t)o * n + o, *dst = cur(Gv_);
+    run([=](const Exec& e) { k_copy3d(e, 1, v, v, src, 0, n, dst, 0, v); });
+  }
   bil(-1.0, ul("klbd"), Gl("ldkc"), 1.0, dyn(Gv_, 0, "bc", {v, v}));
-  k_copy3d(ex, 1, o, o, cur(Ft_), 0, n, cur(Go_), 0, o);
+  {
+    double *src = cur(Ft_), *dst = cur(Go_);
+    run([=](const Exec& e) { k_copy3d(e, 1, o, o, src, 0, n, dst, 0, o); });
+  }
   bil(1.0, ul("ljcd"), Gl("kdlc"), 1.0, dyn(Go_, 0, "kj", {o, o}));
   bil(1.0, t2l("ijac"), dyn(Gv_, 0, "bc", {v, v}), 1.0, X);
   bil(-1.0, t2l("ikab"), dyn(Go_, 0, "kj", {o, o}), 1.0, X);
   // Omega permutation: R_ij^ab += X_ij^ab + X_ji^ba
-  k_sym_add(ex, o, v, cur(X_), r2, 1.0);
+  {
+    double* xx = cur(X_);
+    run([=](const Exec& e) { k_sym_add(e, o, v, xx, r2, 1.0); });
+  }
   (void)Fvo;
   (void)Fvv;
 }
@@ -393,6 +459,79 @@ void Engine::value(const double* t, double* r, double* energy_dev, cc_precision 
   program(false, prec, r);
   if (energy_dev)
     k_energy(ex_, o, v, s_.Govov.p, t_.val.p, t_.val.p + (size_t)o * v, s_.f.p + o, n, energy_dev, scratch_.p);
+}
+
+void Engine::record(OpList& list, bool tan, cc_precision prec, double* out) {
+  rec_ = &list;
+  try {
+    program(tan, prec, out);
+  } catch (...) {
+    rec_ = nullptr;
+    throw;
+  }
+  rec_ = nullptr;
+}
+
+void run_lockstep(const Exec& ex, cc_precision prec, std::vector<OpList>& lists) {
+  bool aligned = true;
+  for (const OpList& l : lists) {
+    if (l.size() != lists[0].size()) aligned = false;
+    for (size_t i = 0; aligned && i < l.size(); ++i)
+      if (l[i].kind != lists[0][i].kind) aligned = false;
+  }
+  if (!aligned) {
+    for (OpList& l : lists)
+      for (Op& op : l) {
+        if (op.kind == Op::KERNEL) op.fn(ex);
+        else contract_group(ex, prec, {op.c});
+      }
+    return;
+  }
+  std::vector<ContractSpec> specs;
+  for (size_t i = 0; i < lists[0].size(); ++i) {
+    if (lists[0][i].kind == Op::KERNEL) {
+      for (OpList& l : lists) l[i].fn(ex);
+      continue;
+    }
+    specs.clear();
+    for (OpList& l : lists) specs.push_back(l[i].c);
+    contract_group(ex, prec, specs);
+  }
+}
+
+void Engine::value_batch(const std::vector<Engine*>& engs, const std::vector<const double*>& t,
+                         const std::vector<double*>& r, const std::vector<double*>& energy_dev, cc_precision prec) {
+  if (engs.empty()) return;
+  std::vector<OpList> lists(engs.size());
+  for (size_t i = 0; i < engs.size(); ++i) {
+    Engine& E = *engs[i];
+    if (E.graphs_on_) E.stage_.mark_stale();
+    else E.stage_.clear();
+    E.first_since_value_ = true;
+    if (t[i] != E.t_.val.p) k_copy(E.ex_, E.s_.namp(), t[i], E.t_.val.p);
+    E.record(lists[i], false, prec, r[i]);
+  }
+  run_lockstep(engs[0]->ex_, prec, lists);
+  for (size_t i = 0; i < engs.size(); ++i) {
+    Engine& E = *engs[i];
+    const int o = E.s_.o, v = E.s_.v;
+    if (energy_dev[i])
+      k_energy(E.ex_, o, v, E.s_.Govov.p, E.t_.val.p, E.t_.val.p + (size_t)o * v, E.s_.f.p + o, E.s_.n, energy_dev[i],
+               E.scratch_.p);
+  }
+}
+
+void Engine::tangent_batch(const std::vector<Engine*>& engs, const std::vector<const double*>& d,
+                           const std::vector<double*>& jd, cc_precision prec) {
+  if (engs.empty()) return;
+  std::vector<OpList> lists(engs.size());
+  for (size_t i = 0; i < engs.size(); ++i) {
+    Engine& E = *engs[i];
+    if (d[i] != E.t_.tan.p) k_copy(E.ex_, E.s_.namp(), d[i], E.t_.tan.p);
+    E.first_since_value_ = false;
+    E.record(lists[i], true, prec, jd[i]);
+  }
+  run_lockstep(engs[0]->ex_, prec, lists);
 }
 
 void Engine::tangent(const double* d, double* jd, cc_precision prec) {

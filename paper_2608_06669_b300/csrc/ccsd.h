@@ -1,6 +1,8 @@
 // Closed-shell DF-CCSD residual engine (value and tangent programs).
 #pragma once
 
+#include <functional>
+
 #include "common.h"
 
 namespace ccpnk {
@@ -32,6 +34,20 @@ int ladder_block_for(int v);
 // about 32 staged copies (4-byte words) of the largest tensors, at most 1 GiB.
 size_t stage_cache_cap(int o, int v, int P);
 
+// One step of a recorded program: a kernel-launch closure or a contraction (see
+// Engine::value_batch).
+struct Op {
+  enum { KERNEL = 0, CONTRACT = 1 };
+  int kind = KERNEL;
+  ContractSpec c;
+  std::function<void(const Exec&)> fn;
+};
+using OpList = std::vector<Op>;
+// Runs the recorded programs of several engines (one stream) step by step: the i-th steps of
+// all of them together, their contractions as one group (contract_group: the tensor-core ones in
+// grouped launches). Programs whose steps do not line up run one after the other.
+void run_lockstep(const Exec& ex, cc_precision prec, std::vector<OpList>& lists);
+
 // Intermediates of one residual evaluation; the tangent program reuses the values.
 class Engine {
  public:
@@ -42,6 +58,12 @@ class Engine {
   void value(const double* t, double* r, double* energy_dev, cc_precision prec);
   // J(t) d at the t of the last value() call.
   void tangent(const double* d, double* jd, cc_precision prec);
+  // value() and tangent() for several engines of one context at once, in lockstep: the same
+  // contraction of every engine in one group (results equal the one-by-one calls).
+  static void value_batch(const std::vector<Engine*>& engs, const std::vector<const double*>& t,
+                          const std::vector<double*>& r, const std::vector<double*>& energy_dev, cc_precision prec);
+  static void tangent_batch(const std::vector<Engine*>& engs, const std::vector<const double*>& d,
+                            const std::vector<double*>& jd, cc_precision prec);
   const Exec& exec() const { return ex_; }
   // Takes the context's current settings (wait limit, staged-operand cache size); a smaller
   // cache drops what it kept.
@@ -89,6 +111,8 @@ class Engine {
   cc_precision graph_prec_ = CC_FP64;
   cudaStream_t cap_stream_ = nullptr;
   DBuf<double> jout_;           // the captured program's output
+  OpList* rec_ = nullptr;       // set: program() records its steps here instead of launching them
+  void record(OpList& list, bool tan, cc_precision prec, double* out);
 };
 
 // Readies cc_energy_noalloc on the current device for this problem: loads its module, looks up

@@ -243,6 +243,9 @@ struct GemmArgs {
 
 // Tensor-core GEMM (gemm_tc.cu): same contract as the FP64 kernel, run on tcgen05.
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag = nullptr);
+// Independent tensor-core GEMMs (no output shared, single-precision kinds) in grouped launches:
+// every problem's tiles in one persistent launch of up to 16 problems per output mode.
+void gemm_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs);
 // One kernel whose bounded wait on an mbarrier that nothing arrives at gives up after
 // ex.wait_ns and sets the device error flag (the self-test of the bounded waits).
 void k_wait_selftest(const Exec& ex);
@@ -275,6 +278,18 @@ TView view_strided(double* p, const char* labels, std::initializer_list<int> ext
 void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
               double beta, const TView& C, const char* tag = nullptr, const StagedOut* so = nullptr,
               const StagedIn* sb = nullptr, StageCache* cache = nullptr, int cache_mask = 0);
+
+// One contraction of a group (contract_group): independent of the others of its group (no
+// output shared, nothing read that another writes).
+struct ContractSpec {
+  double alpha = 1.0, beta = 0.0;
+  TView A, B, C;
+  StageCache* cache = nullptr;
+  int cache_mask = 0;
+};
+// Independent contractions at one precision: those the tensor cores run best share grouped
+// launches (one persistent launch over all their tiles), the rest run one by one.
+void contract_group(const Exec& ex, cc_precision prec, const std::vector<ContractSpec>& specs);
 
 // ---------------------------------------------------------------------------
 // kernels with host launchers (elementwise.cu)

@@ -409,39 +409,40 @@ long long group_size(const std::vector<Mode>& g) {
 
 long long inner_stride(const CIdx& c) { return (c.e1 == 1 && c.e2 == 1) ? c.s0 : c.s2; }
 
+// A contraction too thin for 128 x 256 tensor-core tiles (a short k, or a narrow M or N) costs
+// more in staging, padding and launch latency than it saves: true when the tensor-core run is
+// estimated to be faster than the FP64 kernel (which is more accurate, never less).
+bool tc_faster(const Exec& ex, cc_precision prec, const GemmArgs& g) {
+  const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
+  const int tk = prec == CC_MIXED_BF16X3 || prec == CC_FP64_EMU ? 64 : 32;
+  const double padded = 2.0 * ((g.M + 127) / 128 * 128.0) * ((g.N + 255) / 256 * 256.0) *
+                        ((g.K + tk - 1) / tk * (double)tk) * nseg * g.batch;
+  double t_tc = 12e-6 + padded / 4.5e14 + 8.0 * g.M * (double)g.N * g.batch / 1e12;
+  if (prec == CC_FP64_EMU) {
+    // 36 slice products on kind::f16, the exact partial sums (one per chunk of up to 1024 k,
+    // written and read once in FP32), the digit staging of both operands
+    const double kp = (g.K + 63) / 64 * 64.0, chunks = 36.0 * kp / 1024.0 + 8.0;
+    t_tc = 20e-6 + 36.0 * padded / 1.2e15 + chunks * 8.0 * g.M * (double)g.N * g.batch / 5e12 +
+           ((double)g.M + g.N) * kp * g.batch * 24.0 / 5e12;
+  }
+  // the FP64 kernel's parallelism: 16 x 16 tiles, k split at most 64 ways
+  const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch * std::min(64, std::max(1, g.K / 32));
+  const double flops16 = 2.0 * ((g.M + 15) / 16 * 16.0) * ((g.N + 15) / 16 * 16.0) * g.K * g.batch;
+  double t_f64 = 4e-6 + flops16 / (1.0e12 * std::min(1.0, blocks / ex.sm_count));
+  if ((g.N == 1 || g.M == 1) && (long long)(g.N == 1 ? g.M : g.N) * g.batch >= 256)
+    t_f64 = 4e-6 + 8.0 * (g.N == 1 ? g.M : g.N) * (double)g.K * g.batch / 2e12;  // the FP64 GEMV reads the matrix once
+  return t_tc <= t_f64;
+}
+
 void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   CC_REQUIRE(!((g.so || g.sb) && (prec == CC_FP64 || prec == CC_DF64)), CC_ERR_INVALID, "staged operands need a tensor-core precision");
   if (prec != CC_FP64 && prec != CC_DF64) {
-    // A contraction too thin for 128 x 256 tensor-core tiles (a short k, or a narrow M or
-    // N) costs more in staging, padding and launch latency than it saves: if the FP64
-    // kernel is estimated to be faster it runs there (more accurate, never less).
-    const double flops = 2.0 * g.M * (double)g.N * g.K * g.batch;
-    const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
-    const int tk = prec == CC_MIXED_BF16X3 || prec == CC_FP64_EMU ? 64 : 32;
-    const double padded = 2.0 * ((g.M + 127) / 128 * 128.0) * ((g.N + 255) / 256 * 256.0) *
-                          ((g.K + tk - 1) / tk * (double)tk) * nseg * g.batch;
-    double t_tc = 12e-6 + padded / 4.5e14 + 8.0 * g.M * (double)g.N * g.batch / 1e12;
-    if (prec == CC_FP64_EMU) {
-      // 36 slice products on kind::f16, the exact partial sums (one per chunk of up to 1024 k,
-      // written and read once in FP32), the digit staging of both operands
-      const double kp = (g.K + 63) / 64 * 64.0, chunks = 36.0 * kp / 1024.0 + 8.0;
-      t_tc = 20e-6 + 36.0 * padded / 1.2e15 + chunks * 8.0 * g.M * (double)g.N * g.batch / 5e12 +
-             ((double)g.M + g.N) * kp * g.batch * 24.0 / 5e12;
-    }
-    // the FP64 kernel's parallelism: 16 x 16 tiles, k split at most 64 ways
-    const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch *
-                          std::min(64, std::max(1, g.K / 32));
-    const double flops16 = 2.0 * ((g.M + 15) / 16 * 16.0) * ((g.N + 15) / 16 * 16.0) * g.K * g.batch;
-    double t_f64 = 4e-6 + flops16 / (1.0e12 * std::min(1.0, blocks / ex.sm_count));
-    if ((g.N == 1 || g.M == 1) && (long long)(g.N == 1 ? g.M : g.N) * g.batch >= 256)
-      t_f64 = 4e-6 + 8.0 * (g.N == 1 ? g.M : g.N) * (double)g.K * g.batch / 2e12;  // the FP64 GEMV reads the matrix once
-    if (g.so || g.sb || t_tc <= t_f64) {
+    if (g.so || g.sb || tc_faster(ex, prec, g)) {
       gemm_tc(ex, prec, g, tag);
       return;
     }
     prec = CC_FP64;
-    (void)flops;
   }
   // (a few outputs over a long k stay on the split-k GEMM path, which spreads k over SMs)
   if (prec == CC_FP64 && (g.N == 1 || g.M == 1) && g.K > 0 &&
@@ -540,15 +541,14 @@ bool operator==(const StageKey& a, const StageKey& b) {
          a.nseg == b.nseg && a.seg_lo == b.seg_lo && a.bf == b.bf;
 }
 
-void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
-              double beta, const TView& C, const char* tag, const StagedOut* so, const StagedIn* sb,
-              StageCache* cache, int cache_mask) {
-  std::string auto_tag;  // with the timer on, an untagged contraction is named by its labels
-  if (!tag && ex.prof && ex.prof->on && ex.prof->all) {
-    auto_tag = std::string(A.lab) + "*" + B.lab + ">" + C.lab +
-               (prec == CC_FP64 ? ".f64" : prec == CC_DF64 ? ".df64" : ".tc");
-    tag = auto_tag.c_str();
-  }
+namespace {
+
+// The GEMMs of C = alpha contract(A, B) + beta C: one, or several when modes beyond three
+// spill to a host loop (run in order: later slices of a spilled sum accumulate into C), or
+// none when the output is empty.
+std::vector<GemmArgs> plan_contract(double alpha, const TView& A, const TView& B, double beta, const TView& C,
+                                    const StagedOut* so, const StagedIn* sb, StageCache* cache, int cache_mask) {
+  std::vector<GemmArgs> out;
   auto find = [](const TView& t, char l) {
     for (int d = 0; d < t.nd; ++d)
       if (t.lab[d] == l) return d;
@@ -583,7 +583,7 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
   }
   for (auto* g : {&gb, &gm, &gn})
     for (auto& m : *g)
-      if (m.ext == 0) return;  // empty output
+      if (m.ext == 0) return out;  // empty output
   bool empty_sum = false;
   for (auto& m : gk)
     if (m.ext == 0) empty_sum = true;
@@ -648,7 +648,7 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
     gi.B = B.p + ob;
     gi.C = C.p + oc;
     if (!first_k) gi.beta = 1.0;
-    launch_gemm(ex, prec, gi, tag);
+    out.push_back(gi);
     int q = nl - 1;
     while (q >= 0) {
       if (++idx[q] < loops[q].ext) break;
@@ -657,6 +657,36 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
     }
     if (q < 0) break;
   }
+  return out;
+}
+
+}  // namespace
+
+void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, const TView& B,
+              double beta, const TView& C, const char* tag, const StagedOut* so, const StagedIn* sb,
+              StageCache* cache, int cache_mask) {
+  std::string auto_tag;  // with the timer on, an untagged contraction is named by its labels
+  if (!tag && ex.prof && ex.prof->on && ex.prof->all) {
+    auto_tag = std::string(A.lab) + "*" + B.lab + ">" + C.lab +
+               (prec == CC_FP64 ? ".f64" : prec == CC_DF64 ? ".df64" : ".tc");
+    tag = auto_tag.c_str();
+  }
+  for (const GemmArgs& g : plan_contract(alpha, A, B, beta, C, so, sb, cache, cache_mask)) launch_gemm(ex, prec, g, tag);
+}
+
+void contract_group(const Exec& ex, cc_precision prec, const std::vector<ContractSpec>& specs) {
+  const bool tc = prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3;
+  std::vector<GemmArgs> grouped;
+  for (const ContractSpec& c : specs) {
+    std::vector<GemmArgs> gs = plan_contract(c.alpha, c.A, c.B, c.beta, c.C, nullptr, nullptr, c.cache, c.cache_mask);
+    if (tc && gs.size() == 1 && gs[0].M > 0 && gs[0].N > 0 && gs[0].batch > 0 && gs[0].K > 0 &&
+        tc_faster(ex, prec, gs[0])) {
+      grouped.push_back(gs[0]);
+    } else {
+      for (const GemmArgs& g : gs) launch_gemm(ex, prec, g, nullptr);
+    }
+  }
+  if (!grouped.empty()) gemm_tc_group(ex, prec, grouped);
 }
 
 }  // namespace ccpnk

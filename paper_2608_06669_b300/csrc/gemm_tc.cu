@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
+#include <memory>
 
 #include "common.h"
 
@@ -455,6 +457,28 @@ __device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int
   }
 }
 
+// The problems of one launch: one contraction, or several independent contractions (a
+// grouped launch) that share the tile shape, the operand type and the output mode. Their tiles
+// are numbered consecutively (tile0 holds the prefix sums), and every CTA walks the combined
+// tile list. Passed by value as a __grid_constant__ parameter, so the tensor maps live in the
+// parameter space that TMA reads.
+template <int MAXP>
+struct TcGroup {
+  CUtensorMap tmA[MAXP];
+  CUtensorMap tmB[MAXP];
+  TcArgs args[MAXP];
+  int tile0[MAXP + 1];
+  int nprob;
+};
+constexpr int GROUP_MAX = 16;  // problems of a grouped launch (about 7 KB of parameters)
+
+// the problem that owns global tile t, searched onward from the previous one (t only grows)
+template <int MAXP>
+__device__ __forceinline__ int group_problem(const TcGroup<MAXP>& G, int t, int p) {
+  while (p + 1 < G.nprob && t >= G.tile0[p + 1]) ++p;
+  return p;
+}
+
 // shared memory: STAGES x (A tile, B tile), the epilogue's turn-around tiles, barriers
 constexpr uint32_t EP_FLOATS = 32 * 33;
 constexpr size_t SMEM_USED =
@@ -472,9 +496,8 @@ constexpr size_t SMEM_BYTES = 1024 + SMEM_USED;
 //   warps 2-9: epilogue (TMEM lane quadrant = warp % 4, two warps per quadrant on the two
 //              column halves), releasing an accumulator as soon as it has been read, so the
 //              next tile's MMAs overlap this tile's stores
-template <bool BF, int EPI>
-__global__ void __launch_bounds__(THREADS, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
+template <bool BF, int EPI, int MAXP>
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ TcGroup<MAXP> G) {
   constexpr int TK = Elt<BF>::TK, UK = Elt<BF>::UK;
   using T = typename Elt<BF>::T;
   extern __shared__ uint8_t smem_raw[];
@@ -510,43 +533,49 @@ __global__ void __launch_bounds__(THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
+  const int total = G.tile0[G.nprob];
+  const unsigned long long wait_ns = G.args[0].wait_ns;
 
   if (warp == 0) {
     if (lane == 0) {
       uint32_t q = 0;  // pipeline slot counter, continued across tiles
-      for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+      int p = 0;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        p = group_problem(G, t, p);
+        const TcArgs& g = G.args[p];
         int sp, bz, m0, n0, kA0, kB0, nkb;
-        tile_coords(g, t, sp, bz, m0, n0, kA0, kB0, nkb);
+        tile_coords(g, t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
         for (int kb = 0; kb < nkb; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
-          if (!mbar_wait(empty0 + 8 * s, ph ^ 1, g.wait_ns)) { ok = false; break; }
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1, wait_ns)) { ok = false; break; }
           mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
-          tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, (kA0 + kb) * TK, m0, bz);
-          tma_load_3d(smem_u32(sB + s * B_BYTES), &tmB, full0 + 8 * s, (kB0 + kb) * TK, n0, bz);
+          tma_load_3d(smem_u32(sA + s * A_BYTES), &G.tmA[p], full0 + 8 * s, (kA0 + kb) * TK, m0, bz);
+          tma_load_3d(smem_u32(sB + s * B_BYTES), &G.tmB[p], full0 + 8 * s, (kB0 + kb) * TK, n0, bz);
         }
       }
       // never leave with copies in flight: the last loads issued must have landed (bounded)
       for (uint32_t r = q > (uint32_t)STAGES ? q - STAGES : 0; r < q; ++r)
-        if (!mbar_wait(full0 + 8 * (r % STAGES), (r / STAGES) & 1, g.wait_ns)) ok = false;
+        if (!mbar_wait(full0 + 8 * (r % STAGES), (r / STAGES) & 1, wait_ns)) ok = false;
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
       uint32_t q = 0;
-      int it = 0;
-      for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x, ++it) {
+      int it = 0, p = 0;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
         const int acc = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
-        if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, g.wait_ns)) { ok = false; break; }
+        if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, wait_ns)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * TN);
+        p = group_problem(G, t, p);
         int sp, bz, m0, n0, kA0, kB0, nkb;
-        tile_coords(g, t, sp, bz, m0, n0, kA0, kB0, nkb);
+        tile_coords(G.args[p], t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
         for (int kb = 0; kb < nkb; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
-          if (!mbar_wait(full0 + 8 * s, ph, g.wait_ns)) { ok = false; break; }
+          if (!mbar_wait(full0 + 8 * s, ph, wait_ns)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
@@ -579,18 +608,20 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     const int quad = warp & 3;          // the TMEM lanes (tile rows) this warp may read
     const int half = (warp - 2) >> 2;   // the half of the tile's columns it stores
-    const float alpha_f = (float)g.alpha;
     float* tile = ep + (warp - 2) * EP_FLOATS;
-    int it = 0;
-    for (int t = blockIdx.x; t < g.tiles; t += gridDim.x, ++it) {
+    int it = 0, p = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      bool got = mbar_wait(tfull0 + 8 * acc, use & 1, g.wait_ns);
+      bool got = mbar_wait(tfull0 + 8 * acc, use & 1, wait_ns);
       got = __all_sync(0xffffffffu, got);
       if (!got) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      p = group_problem(G, t, p);
+      const TcArgs& g = G.args[p];
+      const float alpha_f = (float)g.alpha;
       int sp, bz, m0, n0, kA0, kB0, nkb;
-      tile_coords(g, t, sp, bz, m0, n0, kA0, kB0, nkb);
+      tile_coords(g, t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
       // each lane locates one of the warp's 32 rows once; the store loop broadcasts them
       const int my_row = m0 + quad * 32 + lane;
       long long my_off = -1;
@@ -657,7 +688,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
     }
   }
-  if (!ok) atomicExch(g.err, 1);
+  if (!ok) atomicExch(G.args[0].err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -709,10 +740,36 @@ CUtensorMap make_map(const void* base, int k_pad, int rows_pad, int batch, int b
 
 namespace {
 
+// The dynamic shared-memory opt-in is per device and per kernel instance; server threads may
+// race here, so the per-device bits are atomic.
+template <typename K>
+void ensure_smem_attr(K kern, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  CC_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(done.load() & bit)) {
+    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    done.fetch_or(bit);
+  }
+}
+
+// A tensor-core contraction made ready to launch: operands staged, tensor maps and tile
+// arguments set, split-k partial buffer allocated. It is launched alone or in a group with
+// other jobs of the same operand type and output mode.
 template <bool BF>
-void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
+struct TcJob {
+  GemmArgs g{};
+  CUtensorMap mA, mB;
+  TcArgs a{};
+  int epi = EPI_F64;
+  DBuf<double> stA, stB, part;
+};
+
+template <bool BF>
+void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>& job) {
   using T = typename Elt<BF>::T;
   constexpr int TK = Elt<BF>::TK;
+  job.g = g;
   const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
   const int k_pad = (g.K + TK - 1) / TK * TK;
   // the split precisions stage [hi|hi|lo] against [hi|lo|hi] along a three times longer k
@@ -759,8 +816,7 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
     ex.count();
     return reinterpret_cast<T*>(dst);
   };
-  DBuf<double> stA, stB;
-  T* fA = stage(1, g.A, g.am, g.ak, g.ab, g.M, rowsA, nseg == 3 ? 0b100 : 0, stA);
+  T* fA = stage(1, g.A, g.am, g.ak, g.ab, g.M, rowsA, nseg == 3 ? 0b100 : 0, job.stA);
   T* fB = nullptr;
   int rowsBmap = rowsB;
   if (g.sb) {
@@ -770,13 +826,13 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
     fB = static_cast<T*>(const_cast<void*>(g.sb->base));
     rowsBmap = g.sb->rows_pad;
   } else {
-    fB = stage(2, g.B, g.bn, g.bk, g.bb, g.N, rowsB, nseg == 3 ? 0b010 : 0, stB);
+    fB = stage(2, g.B, g.bn, g.bk, g.bb, g.N, rowsB, nseg == 3 ? 0b010 : 0, job.stB);
   }
   CC_CUDA(cudaGetLastError());
   CC_REQUIRE(!g.so || g.beta == 0.0, CC_ERR_INVALID, "a staged output cannot accumulate");
-  CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM, BF);
-  CUtensorMap mB = make_map(fB, kk, rowsBmap, g.batch, TN, BF);
-  TcArgs a;
+  job.mA = make_map(fA, kk, rowsA, g.batch, TM, BF);
+  job.mB = make_map(fB, kk, rowsBmap, g.batch, TN, BF);
+  TcArgs& a = job.a;
   a.M = g.M;
   a.N = g.N;
   a.kblocks = kk / TK;
@@ -831,55 +887,109 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   a.cs_kpad = g.so ? g.so->kpad : 0;
   a.cs_nseg = g.so ? g.so->nseg : 0;
   a.cs_seglo = g.so ? g.so->seg_lo : 0;
-  DBuf<double> part;
   a.part = nullptr;
   if (splits > 1) {
     const size_t np = (size_t)splits * g.batch * g.M * g.N;
-    part.alloc(ex.pool, (np + 1) / 2);
-    a.part = reinterpret_cast<float*>(part.p);
+    job.part.alloc(ex.pool, (np + 1) / 2);
+    a.part = reinterpret_cast<float*>(job.part.p);
   }
   // the epilogue's output mode is a template parameter, so its store loop has no run-time
   // branching on the layout
-  int epi = EPI_F64;
+  job.epi = EPI_F64;
   if (splits > 1) {
-    epi = EPI_PART;
+    job.epi = EPI_PART;
   } else if (g.so) {
     CC_REQUIRE((g.so->nseg == 1 && g.so->seg_lo == 0) || (g.so->nseg == 3 && g.so->seg_lo == 0b010), CC_ERR_INVALID,
                "staged output layout not supported by the tensor-core epilogue");
-    epi = g.so->nseg == 3 ? EPI_STAGED3 : EPI_STAGED1;
+    job.epi = g.so->nseg == 3 ? EPI_STAGED3 : EPI_STAGED1;
   }
-  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
-      epi == EPI_PART      ? gemm_tc_kernel<BF, EPI_PART>
-      : epi == EPI_STAGED1 ? gemm_tc_kernel<BF, EPI_STAGED1>
-      : epi == EPI_STAGED3 ? gemm_tc_kernel<BF, EPI_STAGED3>
-                           : gemm_tc_kernel<BF, EPI_F64>;
-  // the dynamic shared-memory opt-in is per device and per kernel; server threads may race here
-  static std::atomic<uint64_t> attr_done[4];
-  int dev = 0;
-  CC_CUDA(cudaGetDevice(&dev));
-  const uint64_t bit = 1ull << (dev & 63);
-  if (!(attr_done[epi].load() & bit)) {
-    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    attr_done[epi].fetch_or(bit);
+}
+
+// One launch over n jobs of one output mode (n <= MAXP): their tiles numbered consecutively,
+// one persistent CTA per SM at most.
+template <bool BF, int EPI, int MAXP>
+void tc_launch_group(const Exec& ex, TcJob<BF>* const* jobs, int n) {
+  static std::atomic<uint64_t> attr_done{0};
+  auto kern = gemm_tc_kernel<BF, EPI, MAXP>;
+  ensure_smem_attr(kern, attr_done);
+  TcGroup<MAXP> G;
+  memset(&G, 0, sizeof(G));
+  G.nprob = n;
+  G.tile0[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    G.tmA[i] = jobs[i]->mA;
+    G.tmB[i] = jobs[i]->mB;
+    G.args[i] = jobs[i]->a;
+    CC_REQUIRE((long long)G.tile0[i] + jobs[i]->a.tiles < (1LL << 31), CC_ERR_INVALID, "grouped launch: too many tiles");
+    G.tile0[i + 1] = G.tile0[i] + jobs[i]->a.tiles;
   }
-  const int grid = std::min(a.tiles, ex.sm_count);  // persistent: at most one CTA per SM
-  cudaEvent_t ev = nullptr;
-  if (ex.timing(tag)) ex.mark_begin(&ev);
-  kern<<<grid, THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
+  const int grid = std::min(G.tile0[n], ex.sm_count);
+  if (grid <= 0) return;
+  kern<<<grid, THREADS, SMEM_BYTES, ex.stream>>>(G);
   ex.count();
   CC_CUDA(cudaGetLastError());
-  if (splits > 1) {
-    // short outputs are cut into warp-sized pieces so that enough warps share the reads
-    const size_t rows = (size_t)g.batch * g.M;
-    const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
-    const size_t items = rows * ((g.N + piece - 1) / piece);
-    const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
-    tc_splitk_reduce_kernel<T><<<rblocks, 256, 0, ex.stream>>>(g, a.part, splits, static_cast<T*>(a.Cs), a.cs_kpad,
-                                                               a.cs_nseg, a.cs_seglo, piece);
-    ex.count();
-    CC_CUDA(cudaGetLastError());
+}
+
+template <bool BF, int MAXP>
+void tc_launch(const Exec& ex, int epi, TcJob<BF>* const* jobs, int n) {
+  switch (epi) {
+    case EPI_PART: tc_launch_group<BF, EPI_PART, MAXP>(ex, jobs, n); break;
+    case EPI_STAGED1: tc_launch_group<BF, EPI_STAGED1, MAXP>(ex, jobs, n); break;
+    case EPI_STAGED3: tc_launch_group<BF, EPI_STAGED3, MAXP>(ex, jobs, n); break;
+    default: tc_launch_group<BF, EPI_F64, MAXP>(ex, jobs, n); break;
   }
+}
+
+// split-k: the partial sums of a finished job added in a fixed order into C (or its staging)
+template <bool BF>
+void tc_finish(const Exec& ex, TcJob<BF>& job) {
+  using T = typename Elt<BF>::T;
+  const GemmArgs& g = job.g;
+  if (job.a.splits <= 1) return;
+  // short outputs are cut into warp-sized pieces so that enough warps share the reads
+  const size_t rows = (size_t)g.batch * g.M;
+  const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
+  const size_t items = rows * ((g.N + piece - 1) / piece);
+  const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
+  tc_splitk_reduce_kernel<T><<<rblocks, 256, 0, ex.stream>>>(g, job.a.part, job.a.splits, static_cast<T*>(job.a.Cs),
+                                                             job.a.cs_kpad, job.a.cs_nseg, job.a.cs_seglo, piece);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+}
+
+template <bool BF>
+void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
+  TcJob<BF> job;
+  tc_prepare<BF>(ex, prec, g, job);
+  cudaEvent_t ev = nullptr;
+  if (ex.timing(tag)) ex.mark_begin(&ev);
+  TcJob<BF>* one = &job;
+  tc_launch<BF, 1>(ex, job.epi, &one, 1);
+  tc_finish<BF>(ex, job);
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
+}
+
+// Independent contractions of one precision in as few launches as possible: every job is
+// prepared (operands staged), jobs of the same output mode share launches of up to GROUP_MAX
+// problems, then the split-k reductions run.
+template <bool BF>
+void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs) {
+  std::vector<std::unique_ptr<TcJob<BF>>> jobs;
+  for (const auto& g : gs) {
+    jobs.emplace_back(new TcJob<BF>());
+    tc_prepare<BF>(ex, prec, g, *jobs.back());
+  }
+  for (int epi = 0; epi < 4; ++epi) {
+    std::vector<TcJob<BF>*> sel;
+    for (auto& j : jobs)
+      if (j->epi == epi) sel.push_back(j.get());
+    for (size_t i = 0; i < sel.size(); i += GROUP_MAX) {
+      const int n = (int)std::min<size_t>(GROUP_MAX, sel.size() - i);
+      if (n == 1) tc_launch<BF, 1>(ex, epi, &sel[i], 1);
+      else tc_launch<BF, GROUP_MAX>(ex, epi, &sel[i], n);
+    }
+  }
+  for (auto& j : jobs) tc_finish<BF>(ex, *j);
 }
 
 // FP64-accurate contraction on the tensor cores (see oz_stage_kernel): stage both operands
@@ -956,18 +1066,12 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   const size_t np = (size_t)nsplit * g.batch * g.M * g.N;
   DBuf<double> part(ex.pool, (np + 1) / 2);
   a.part = reinterpret_cast<float*>(part.p);
-  auto kern = gemm_tc_kernel<true, EPI_PART>;
-  static std::atomic<uint64_t> attr_done{0};
-  int dev = 0;
-  CC_CUDA(cudaGetDevice(&dev));
-  const uint64_t bit = 1ull << (dev & 63);
-  if (!(attr_done.load() & bit)) {
-    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    attr_done.fetch_or(bit);
-  }
-  kern<<<(int)std::min<long long>(tiles, ex.sm_count), THREADS, SMEM_BYTES, ex.stream>>>(mA, mB, a);
-  ex.count();
-  CC_CUDA(cudaGetLastError());
+  TcJob<true> job;
+  job.mA = mA;
+  job.mB = mB;
+  job.a = a;
+  TcJob<true>* one = &job;
+  tc_launch_group<true, EPI_PART, 1>(ex, &one, 1);
   // the fixed-point sum's bound: the level-L chunk sums add up to (L - 1) k_pad (2^beta - 1)^2
   double bound = 0.0;
   for (int L = 2; L <= OZ_S + 1; ++L)
@@ -991,6 +1095,24 @@ void k_wait_selftest(const Exec& ex) {
   wait_selftest_kernel<<<1, 32, 0, ex.stream>>>(ex.dev_flag, ex.wait_ns);
   ex.count();
   CC_CUDA(cudaGetLastError());
+}
+
+void gemm_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs) {
+  CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3, CC_ERR_INVALID,
+             "grouped launches run the single-precision tensor-core kinds");
+  CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
+  std::vector<GemmArgs> todo;
+  for (const auto& g : gs) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) continue;
+    if (g.K <= 0) {
+      gemm_tc(ex, prec, g);  // C = beta C
+      continue;
+    }
+    todo.push_back(g);
+  }
+  if (todo.empty()) return;
+  if (prec == CC_MIXED_BF16X3) run_tc_group<true>(ex, prec, todo);
+  else run_tc_group<false>(ex, prec, todo);
 }
 
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {

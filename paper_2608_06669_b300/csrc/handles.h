@@ -1,8 +1,11 @@
 // The opaque handles of the C ABI (cc_ctx, cc_sys), shared by the sources that implement it.
 #pragma once
 
+#include <atomic>
+#include <functional>
 #include <memory>
 #include <string>
+#include <vector>
 
 #include "solver.h"
 
@@ -41,6 +44,11 @@ struct cc_sys {
 };
 
 namespace ccpnk {
+// cc_solve_batch with a callback notify(k, status), called once problem k's amplitudes are in
+// t1s[k] / t2s[k] and its report in reports[k], and per-problem cancellation flags.
+int solve_batch_notify(cc_ctx* ctx, int nsys, cc_sys* const* sys, const cc_solve_opts* opts, double* const* t1s,
+                       double* const* t2s, cc_report* reports, const std::function<void(int, int)>& notify,
+                       const std::vector<const std::atomic<int>*>* cancel);
 // cc_solve with a cancellation flag that another thread may set (the server's cancel).
 int solve_cancellable(cc_ctx* ctx, cc_sys* sys, const cc_solve_opts* opts, double* t1, double* t2, int use_guess,
                       cc_report* report, const std::atomic<int>* cancel);

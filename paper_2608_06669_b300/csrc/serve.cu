@@ -75,11 +75,41 @@ struct cc_server {
   size_t in_use = 0;
   int running = 0, max_running = 0;
   bool stop = false;
+  int group_max = 1;  // > 1: a slot solves up to this many compatible requests together
   std::vector<std::thread> workers;
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
 
 namespace {
+
+// Requests a slot may solve together: NK or PNK with identical options (so one lockstep batch
+// runs them all exactly as each would run alone).
+bool groupable(const Request& a, const Request& b) {
+  const cc_solve_opts &x = a.opts, &y = b.opts;
+  return (x.method == CC_NK || x.method == CC_PNK) && x.method == y.method && x.prec == y.prec && x.tol == y.tol &&
+         x.max_outer == y.max_outer && x.m_max == y.m_max && x.gamma == y.gamma && x.alpha == y.alpha &&
+         x.eta_max == y.eta_max && x.jvp_fd == 0 && y.jvp_fd == 0 && x.inner_rtol == y.inner_rtol &&
+         x.inner_max == y.inner_max && x.af_direct == y.af_direct && x.ccd == y.ccd &&
+         x.max_seconds == y.max_seconds && x.outer_prec == y.outer_prec;
+}
+
+// Posts a finished request's result (called with the server's lock held).
+void post(cc_server* srv, Request* r, int status, const cc_report& rep, std::vector<double>& t1,
+          std::vector<double>& t2, const std::string& err) {
+  r->status = status;
+  r->report = rep;
+  r->t1.swap(t1);
+  r->t2.swap(t2);
+  r->err = err;
+  r->t_finish = srv->now();
+  r->done = true;
+  r->fock.clear();
+  r->fock.shrink_to_fit();
+  r->B.clear();
+  r->B.shrink_to_fit();
+  srv->in_use -= r->footprint;
+  srv->running -= 1;
+}
 
 void worker_main(cc_server* srv, int slot) {
   (void)slot;
@@ -87,7 +117,7 @@ void worker_main(cc_server* srv, int slot) {
   cc_ctx* ctx = nullptr;
   int st = cc_ctx_create(&ctx, srv->device, 0, nullptr);
   for (;;) {
-    Request* r = nullptr;
+    std::vector<Request*> batch;
     {
       std::unique_lock<std::mutex> lk(srv->mu);
       // FIFO admission: the oldest request goes first once its memory estimate fits
@@ -98,45 +128,92 @@ void worker_main(cc_server* srv, int slot) {
         return srv->budget == 0 || srv->in_use + h->footprint <= srv->budget || srv->running == 0;
       });
       if (srv->stop) break;
-      r = srv->queue.front();
+      batch.push_back(srv->queue.front());
       srv->queue.pop_front();
-      srv->in_use += r->footprint;
-      srv->running += 1;
-      srv->max_running = std::max(srv->max_running, srv->running);
-      r->t_admit = srv->now();
-    }
-    int status = CC_ERR_CUDA;
-    std::string err;
-    cc_report rep{};
-    std::vector<double> t1((size_t)r->o * r->v), t2((size_t)r->o * r->o * r->v * r->v);
-    if (st == CC_OK && ctx) {
-      cc_sys* sys = nullptr;
-      status = cc_sys_create(ctx, r->o, r->v, r->naux, r->fock.data(), r->B.data(), &sys);
-      if (status == CC_OK) {
-        status = ccpnk::solve_cancellable(ctx, sys, &r->opts, t1.data(), t2.data(), 0, &rep, &r->cancel);
-        cc_sys_destroy(sys);
+      size_t fp = batch[0]->footprint;
+      // grouped mode: later waiting requests that can run in the same lockstep batch and fit
+      for (auto it = srv->queue.begin(); (int)batch.size() < srv->group_max && it != srv->queue.end();) {
+        Request* c = *it;
+        if (groupable(*batch[0], *c) && (srv->budget == 0 || srv->in_use + fp + c->footprint <= srv->budget)) {
+          fp += c->footprint;
+          batch.push_back(c);
+          it = srv->queue.erase(it);
+        } else {
+          ++it;
+        }
       }
+      for (Request* r : batch) {
+        srv->in_use += r->footprint;
+        srv->running += 1;
+        r->t_admit = srv->now();
+      }
+      srv->max_running = std::max(srv->max_running, srv->running);
+    }
+    const int nb = (int)batch.size();
+    std::vector<std::vector<double>> t1(nb), t2(nb);
+    for (int k = 0; k < nb; ++k) {
+      t1[k].assign((size_t)batch[k]->o * batch[k]->v, 0.0);
+      t2[k].assign((size_t)batch[k]->o * batch[k]->o * batch[k]->v * batch[k]->v, 0.0);
+    }
+    if (st != CC_OK || !ctx) {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      for (int k = 0; k < nb; ++k) post(srv, batch[k], CC_ERR_CUDA, cc_report{}, t1[k], t2[k], "no device context for this slot");
+      srv->cv.notify_all();
+      continue;
+    }
+    // the problems (a request whose input the library rejects fails on its own)
+    std::vector<cc_sys*> sys(nb, nullptr);
+    std::vector<int> live;
+    for (int k = 0; k < nb; ++k) {
+      Request* r = batch[k];
+      const int cs = cc_sys_create(ctx, r->o, r->v, r->naux, r->fock.data(), r->B.data(), &sys[k]);
+      if (cs == CC_OK) {
+        live.push_back(k);
+      } else {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        post(srv, r, cs, cc_report{}, t1[k], t2[k], cc_last_error(ctx));
+        srv->cv.notify_all();
+      }
+    }
+    if (live.size() == 1) {
+      const int k = live[0];
+      Request* r = batch[k];
+      cc_report rep{};
+      const int status = ccpnk::solve_cancellable(ctx, sys[k], &r->opts, t1[k].data(), t2[k].data(), 0, &rep, &r->cancel);
+      std::string err;
       if (status < 0 && status != CC_ERR_NOT_CONVERGED && status != CC_ERR_DIVERGED && status != CC_ERR_CANCELLED)
         err = cc_last_error(ctx);
-    } else {
-      err = "no device context for this slot";
-    }
-    {
       std::lock_guard<std::mutex> lk(srv->mu);
-      r->status = status;
-      r->report = rep;
-      r->t1.swap(t1);
-      r->t2.swap(t2);
-      r->err = err;
-      r->t_finish = srv->now();
-      r->done = true;
-      r->fock.clear();
-      r->fock.shrink_to_fit();
-      r->B.clear();
-      r->B.shrink_to_fit();
-      srv->in_use -= r->footprint;
-      srv->running -= 1;
+      post(srv, r, status, rep, t1[k], t2[k], err);
+    } else if (!live.empty()) {
+      // one lockstep batch; each request is posted as soon as it has finished
+      const int nl = (int)live.size();
+      std::vector<cc_sys*> ls;
+      std::vector<double*> p1, p2;
+      std::vector<const std::atomic<int>*> cancels;
+      std::vector<cc_report> reps(nl);
+      for (int k : live) {
+        ls.push_back(sys[k]);
+        p1.push_back(t1[k].data());
+        p2.push_back(t2[k].data());
+        cancels.push_back(&batch[k]->cancel);
+      }
+      auto notify = [&](int j, int status) {
+        const int k = live[j];
+        std::lock_guard<std::mutex> lk(srv->mu);
+        post(srv, batch[k], status, reps[j], t1[k], t2[k], "");
+        srv->cv.notify_all();
+      };
+      const int bs = ccpnk::solve_batch_notify(ctx, nl, ls.data(), &batch[live[0]]->opts, p1.data(), p2.data(),
+                                               reps.data(), notify, &cancels);
+      if (bs != CC_OK) {  // the batch itself failed: every request not yet posted gets its error
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (int k : live)
+          if (!batch[k]->done) post(srv, batch[k], bs, cc_report{}, t1[k], t2[k], cc_last_error(ctx));
+      }
     }
+    for (cc_sys* s : sys)
+      if (s) cc_sys_destroy(s);
     srv->cv.notify_all();
   }
   if (ctx) cc_ctx_destroy(ctx);
@@ -217,6 +294,13 @@ int cc_serve_poll(cc_server* srv, uint64_t ticket, cc_report* report, double* t1
   r->t2.clear();
   r->t2.shrink_to_fit();
   return r->status;
+}
+
+int cc_server_set_grouping(cc_server* srv, int group_max) {
+  if (!srv || group_max < 1 || group_max > 64) return CC_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->group_max = group_max;
+  return CC_OK;
 }
 
 int cc_serve_cancel(cc_server* srv, uint64_t ticket) {

@@ -70,70 +70,96 @@ double host_dot(const Exec& ex, size_t n, const double* x, const double* y, doub
   return h;
 }
 
-int gmres(const Exec& ex, size_t n, const LinOp& op, const double* b, double* x, double rtol, int m_max,
-          double* V, double* small, double* scratch, double* est_out) {
+Gmres::Gmres(const Exec& ex, size_t n, int m_max, double* V, double* small, double* scratch)
+    : ex_(ex), n_(n), m_(m_max), V_(V), small_(small), scratch_(scratch) {}
+
+bool Gmres::start(const double* b, double* x, double rtol) {
   // small: device array of >= 2 * (m_max + 1) + 2 doubles
-  k_dot(ex, n, b, b, small, scratch);
+  x_ = x;
+  rtol_ = rtol;
+  j_ = 0;
+  k_dot(ex_, n_, b, b, small_, scratch_);
   double beta2;
-  d2h(ex, &beta2, small, 1);
-  double beta = std::sqrt(beta2);
-  k_fill(ex, n, 0.0, x);
-  if (est_out) *est_out = beta;
-  if (beta == 0.0 || m_max <= 0) return 0;
-  k_axpby(ex, n, 1.0 / beta, b, 0.0, V);
-  std::vector<double> H((size_t)(m_max + 1) * m_max, 0.0), cs(m_max), sn(m_max), g(m_max + 1, 0.0);
-  auto Hc = [&](int r, int c) -> double& { return H[(size_t)c * (m_max + 1) + r]; };
-  g[0] = beta;
-  std::vector<double> hh(2 * (m_max + 1) + 1);
-  int steps = 0;
-  double est = beta;
-  for (int j = 0; j < m_max; ++j) {
-    double* w = V + (size_t)(j + 1) * n;
-    op(V + (size_t)j * n, w);
-    // CGS2: two passes of classical Gram-Schmidt against V[0..j]
-    double* h1 = small;
-    double* h2 = small + (m_max + 1);
-    double* nn = small + 2 * (m_max + 1);
-    k_multi_dot(ex, j + 1, n, V, n, w, h1, scratch);
-    k_multi_axpy(ex, j + 1, n, V, n, h1, w);
-    k_multi_dot(ex, j + 1, n, V, n, w, h2, scratch);
-    k_multi_axpy(ex, j + 1, n, V, n, h2, w);
-    k_dot(ex, n, w, w, nn, scratch);
-    d2h(ex, hh.data(), small, 2 * (m_max + 1) + 1);
-    for (int i = 0; i <= j; ++i) Hc(i, j) = hh[i] + hh[(m_max + 1) + i];
-    double hn = std::sqrt(std::max(hh[2 * (m_max + 1)], 0.0));
-    Hc(j + 1, j) = hn;
-    // previous Givens rotations on the new column, then a new one for H[j+1][j]
-    for (int i = 0; i < j; ++i) {
-      double a = Hc(i, j), c = Hc(i + 1, j);
-      Hc(i, j) = cs[i] * a + sn[i] * c;
-      Hc(i + 1, j) = -sn[i] * a + cs[i] * c;
-    }
-    double a = Hc(j, j), c = Hc(j + 1, j);
-    double r = std::hypot(a, c);
-    cs[j] = r > 0 ? a / r : 1.0;
-    sn[j] = r > 0 ? c / r : 0.0;
-    Hc(j, j) = r;
-    Hc(j + 1, j) = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    est = std::fabs(g[j + 1]);
-    steps = j + 1;
-    if (hn > 0.0) k_scale(ex, n, 1.0 / hn, w);
-    if (!(est > rtol * beta) || hn == 0.0 || !std::isfinite(est)) break;
+  d2h(ex_, &beta2, small_, 1);
+  beta_ = std::sqrt(beta2);
+  est_ = beta_;
+  k_fill(ex_, n_, 0.0, x);
+  if (beta_ == 0.0 || m_ <= 0) return false;
+  k_axpby(ex_, n_, 1.0 / beta_, b, 0.0, V_);
+  H_.assign((size_t)(m_ + 1) * m_, 0.0);
+  cs_.assign(m_, 0.0);
+  sn_.assign(m_, 0.0);
+  g_.assign(m_ + 1, 0.0);
+  g_[0] = beta_;
+  hh_.assign(2 * (m_ + 1) + 1, 0.0);
+  return true;
+}
+
+bool Gmres::step() {
+  auto Hc = [&](int r, int c) -> double& { return H_[(size_t)c * (m_ + 1) + r]; };
+  const int j = j_;
+  double* w = V_ + (size_t)(j + 1) * n_;
+  // CGS2: two passes of classical Gram-Schmidt against V[0..j]
+  double* h1 = small_;
+  double* h2 = small_ + (m_ + 1);
+  double* nn = small_ + 2 * (m_ + 1);
+  k_multi_dot(ex_, j + 1, n_, V_, n_, w, h1, scratch_);
+  k_multi_axpy(ex_, j + 1, n_, V_, n_, h1, w);
+  k_multi_dot(ex_, j + 1, n_, V_, n_, w, h2, scratch_);
+  k_multi_axpy(ex_, j + 1, n_, V_, n_, h2, w);
+  k_dot(ex_, n_, w, w, nn, scratch_);
+  d2h(ex_, hh_.data(), small_, 2 * (m_ + 1) + 1);
+  for (int i = 0; i <= j; ++i) Hc(i, j) = hh_[i] + hh_[(m_ + 1) + i];
+  const double hn = std::sqrt(std::max(hh_[2 * (m_ + 1)], 0.0));
+  Hc(j + 1, j) = hn;
+  // previous Givens rotations on the new column, then a new one for H[j+1][j]
+  for (int i = 0; i < j; ++i) {
+    const double a = Hc(i, j), c = Hc(i + 1, j);
+    Hc(i, j) = cs_[i] * a + sn_[i] * c;
+    Hc(i + 1, j) = -sn_[i] * a + cs_[i] * c;
   }
+  const double a = Hc(j, j), c = Hc(j + 1, j);
+  const double r = std::hypot(a, c);
+  cs_[j] = r > 0 ? a / r : 1.0;
+  sn_[j] = r > 0 ? c / r : 0.0;
+  Hc(j, j) = r;
+  Hc(j + 1, j) = 0.0;
+  g_[j + 1] = -sn_[j] * g_[j];
+  g_[j] = cs_[j] * g_[j];
+  est_ = std::fabs(g_[j + 1]);
+  j_ = j + 1;
+  if (hn > 0.0) k_scale(ex_, n_, 1.0 / hn, w);
+  return j_ < m_ && est_ > rtol_ * beta_ && hn != 0.0 && std::isfinite(est_);
+}
+
+int Gmres::finish() {
+  auto Hc = [&](int r, int c) -> double& { return H_[(size_t)c * (m_ + 1) + r]; };
+  const int steps = j_;
+  if (steps == 0) return 0;
   // back substitution for y, then x = V y
   std::vector<double> y(steps, 0.0);
   for (int i = steps - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int k = i + 1; k < steps; ++k) s -= Hc(i, k) * y[k];
-    y[i] = Hc(i, i) != 0.0 ? s / Hc(i, i) : 0.0;
+    double sum = g_[i];
+    for (int k = i + 1; k < steps; ++k) sum -= Hc(i, k) * y[k];
+    y[i] = Hc(i, i) != 0.0 ? sum / Hc(i, i) : 0.0;
   }
   for (int i = 0; i < steps; ++i) y[i] = -y[i];  // multi_axpy subtracts
-  CC_CUDA(cudaMemcpyAsync(small, y.data(), steps * sizeof(double), cudaMemcpyHostToDevice, ex.stream));
-  k_multi_axpy(ex, steps, n, V, n, small, x);
-  CC_CUDA(cudaStreamSynchronize(ex.stream));  // y lives on the host stack
-  if (est_out) *est_out = est;
+  CC_CUDA(cudaMemcpyAsync(small_, y.data(), steps * sizeof(double), cudaMemcpyHostToDevice, ex_.stream));
+  k_multi_axpy(ex_, steps, n_, V_, n_, small_, x_);
+  CC_CUDA(cudaStreamSynchronize(ex_.stream));  // y lives on the host stack
+  return steps;
+}
+
+int gmres(const Exec& ex, size_t n, const LinOp& op, const double* b, double* x, double rtol, int m_max,
+          double* V, double* small, double* scratch, double* est_out) {
+  Gmres gm(ex, n, m_max, V, small, scratch);
+  if (gm.start(b, x, rtol)) {
+    do {
+      op(gm.in(), gm.out());
+    } while (gm.step());
+  }
+  const int steps = gm.finish();
+  if (est_out) *est_out = gm.est();
   return steps;
 }
 
@@ -494,6 +520,200 @@ int solve(const Exec& ex, System& s, Engine& eng, const cc_solve_opts& opt, doub
     rep->seconds = std::chrono::duration<double>(t_end - t_start).count();
   }
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// several NK / PNK solves in lockstep
+// ---------------------------------------------------------------------------
+int solve_batch(const Exec& ex, const std::vector<System*>& sys, const std::vector<Engine*>& eng,
+                const cc_solve_opts& opt, const std::vector<double*>& t, std::vector<cc_report>& reps,
+                const std::function<void(int, int)>& on_done, const std::vector<const std::atomic<int>*>* cancel) {
+  const int K = (int)sys.size();
+  reps.assign(K, cc_report{});
+  auto cancel_of = [&](int k) -> const std::atomic<int>* { return cancel && (int)cancel->size() > k ? (*cancel)[k] : nullptr; };
+  if ((opt.method != CC_NK && opt.method != CC_PNK) || opt.jvp_fd || K <= 1) {
+    for (int k = 0; k < K; ++k) {
+      const int st = solve(ex, *sys[k], *eng[k], opt, t[k], &reps[k], false, cancel_of(k));
+      if (on_done) on_done(k, st);
+    }
+    return CC_OK;
+  }
+  auto t_start = std::chrono::steady_clock::now();
+  const double inner_rtol = opt.inner_rtol > 0 ? opt.inner_rtol
+                            : (opt.prec == CC_MIXED_TF32 ? 1e-6 : opt.prec == CC_MIXED_BF16X3 ? 1e-7
+                               : opt.prec == CC_MIXED_TF32X3 ? 1e-8 : 1e-12);
+  const int inner_max = opt.inner_max > 0 ? opt.inner_max : 50;
+  const double eta_min = opt.prec == CC_MIXED_TF32 ? 1e-4 : opt.prec == CC_MIXED_BF16X3 ? 1e-5
+                         : opt.prec == CC_MIXED_TF32X3 ? 1e-7 : 1e-10;
+  const int m_max = std::max(1, opt.m_max);
+  const cc_precision outer = opt.outer_prec == CC_DF64 ? CC_DF64 : opt.outer_prec == CC_FP64_EMU ? CC_FP64_EMU : CC_FP64;
+  const bool pre = opt.method == CC_PNK;
+  struct Slot {
+    System* s;
+    Engine* e;
+    double* t;
+    size_t n = 0, n1 = 0;
+    DBuf<double> r, dev, red, symw, z, V, small, sc, jq, delta;
+    SolveStats st;
+    double energy = 0, rn = 0, rn_prev = 0, eta_prev = 0;
+    int status = CC_ERR_NOT_CONVERGED;
+    bool done = false, running = false;
+    std::unique_ptr<Gmres> gm;
+  };
+  std::vector<std::unique_ptr<Slot>> slots;
+  for (int k = 0; k < K; ++k) {
+    std::unique_ptr<Slot> q(new Slot);
+    q->s = sys[k];
+    q->e = eng[k];
+    q->t = t[k];
+    q->n = q->s->namp();
+    q->n1 = (size_t)q->s->o * q->s->v;
+    q->r.alloc(ex.pool, q->n);
+    q->dev.alloc(ex.pool, 16);
+    q->red.alloc(ex.pool, 64 * 1024);
+    q->symw.alloc(ex.pool, opt.prec == CC_FP64 ? 0 : q->n - q->n1);
+    q->z.alloc(ex.pool, q->n);
+    q->V.alloc(ex.pool, (size_t)(m_max + 1) * q->n);
+    q->small.alloc(ex.pool, 2 * (size_t)(m_max + 1) + 8);
+    q->sc.alloc(ex.pool, (size_t)(m_max + 1) * 1024 + 1024);
+    q->jq.alloc(ex.pool, q->n);
+    q->delta.alloc(ex.pool, q->n);
+    q->eta_prev = opt.eta_max;
+    slots.push_back(std::move(q));
+  }
+  // A_F^{-1} of one slot, projected back onto t_ij^ab = t_ji^ba at the tensor-core precisions
+  auto AFinv = [&](Slot& q, const double* b, double* x) {
+    solve_AF(ex, *q.s, b, x, opt.prec, inner_rtol, inner_max, opt.af_direct != 0, &q.st);
+    if (opt.prec != CC_FP64) {
+      const int o = q.s->o, v = q.s->v;
+      k_sym_add(ex, o, v, x + q.n1, q.symw.p, 0.0);
+      k_axpby(ex, q.n - q.n1, 0.5, q.symw.p, 0.0, x + q.n1);
+    }
+  };
+  auto finish = [&](Slot& q, int k) {
+    cc_report& rep = reps[k];
+    rep.energy = q.energy;
+    rep.res_norm = q.rn;
+    rep.newton_iters = q.st.newton_iters;
+    rep.residual_evals = q.st.residual_evals;
+    rep.jvps = q.st.jvps;
+    rep.af_applies = q.st.af_applies;
+    rep.krylov_iters = q.st.krylov_iters;
+    rep.status = q.status;
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    q.done = true;
+    if (on_done) on_done(k, q.status);
+  };
+  // the generalised MP2 start of every problem (as in solve)
+  for (auto& qp : slots) {
+    Slot& q = *qp;
+    const int o = q.s->o, v = q.s->v;
+    k_fill(ex, q.n, 0.0, q.t);
+    if (opt.ccd) {
+      k_fill(ex, q.n1, 0.0, q.r.p);
+    } else {
+      k_copy2d(ex, o, v, q.s->f.p + o, q.s->n, q.r.p, v);
+      k_scale(ex, q.n1, -1.0, q.r.p);
+    }
+    k_ovov_to_oovv(ex, o, v, q.s->Govov.p, q.r.p + q.n1, -1.0);
+    AFinv(q, q.r.p, q.t);
+  }
+  for (int it = 0; it < opt.max_outer; ++it) {
+    std::vector<int> act;
+    for (int k = 0; k < K; ++k)
+      if (!slots[k]->done) act.push_back(k);
+    if (act.empty()) break;
+    // the residuals of every unfinished problem, evaluated together
+    std::vector<Engine*> es;
+    std::vector<const double*> ts;
+    std::vector<double*> rs, eds;
+    for (int k : act) {
+      es.push_back(slots[k]->e);
+      ts.push_back(slots[k]->t);
+      rs.push_back(slots[k]->r.p);
+      eds.push_back(slots[k]->dev.p + 1);
+    }
+    Engine::value_batch(es, ts, rs, eds, outer);
+    const bool late = opt.max_seconds > 0 &&
+                      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > opt.max_seconds;
+    std::vector<int> go;
+    for (int k : act) {
+      Slot& q = *slots[k];
+      if (opt.ccd) k_fill(ex, q.n1, 0.0, q.r.p);
+      q.st.residual_evals++;
+      k_dot(ex, q.n, q.r.p, q.r.p, q.dev.p, q.red.p);
+      double hv[2];
+      d2h(ex, hv, q.dev.p, 2);
+      q.energy = hv[1];
+      q.rn = std::sqrt(std::max(hv[0], 0.0));
+      if (opt.verbose) fprintf(stderr, "[ccpnk] batch %d newton %3d  |R| %.3e  E %.12f\n", k, it, q.rn, q.energy);
+      if (!std::isfinite(q.rn) || q.rn > 1e8) {
+        q.status = CC_ERR_DIVERGED;
+        finish(q, k);
+      } else if (q.rn < opt.tol) {
+        q.status = CC_OK;
+        finish(q, k);
+      } else if (late) {
+        finish(q, k);
+      } else if (cancel_of(k) && cancel_of(k)->load() != 0) {
+        q.status = CC_ERR_CANCELLED;
+        finish(q, k);
+      } else {
+        go.push_back(k);
+      }
+    }
+    // one Newton step for each of the others, their Krylov iterations in lockstep
+    for (int k : go) {
+      Slot& q = *slots[k];
+      q.st.newton_iters++;
+      double eta = opt.eta_max;
+      if (it > 0 && q.rn_prev > 0) {
+        eta = opt.gamma * std::pow(q.rn / q.rn_prev, opt.alpha);
+        const double sg = opt.gamma * std::pow(q.eta_prev, opt.alpha);
+        if (sg > 0.1) eta = std::max(eta, sg);
+      }
+      eta = std::min(std::max(eta, eta_min), opt.eta_max);
+      q.eta_prev = eta;
+      q.rn_prev = q.rn;
+      if (pre) AFinv(q, q.r.p, q.z.p);
+      else k_copy(ex, q.n, q.r.p, q.z.p);
+      q.gm.reset(new Gmres(ex, q.n, m_max, q.V.p, q.small.p, q.sc.p));
+      q.running = q.gm->start(q.z.p, q.delta.p, eta);
+    }
+    while (true) {
+      std::vector<int> run;
+      for (int k : go)
+        if (slots[k]->running) run.push_back(k);
+      if (run.empty()) break;
+      std::vector<Engine*> je;
+      std::vector<const double*> jin;
+      std::vector<double*> jout;
+      for (int k : run) {
+        Slot& q = *slots[k];
+        je.push_back(q.e);
+        jin.push_back(q.gm->in());
+        jout.push_back(pre ? q.jq.p : q.gm->out());
+      }
+      Engine::tangent_batch(je, jin, jout, opt.prec);
+      for (int k : run) {
+        Slot& q = *slots[k];
+        q.st.jvps++;
+        if (opt.ccd) k_fill(ex, q.n1, 0.0, pre ? q.jq.p : q.gm->out());
+        if (pre) AFinv(q, q.jq.p, q.gm->out());
+        q.running = q.gm->step();
+      }
+    }
+    for (int k : go) {
+      Slot& q = *slots[k];
+      q.st.krylov_iters += q.gm->finish();
+      // t <- t - sum_i q_i y_i (Algorithm 1)
+      k_axpby(ex, q.n, -1.0, q.delta.p, 1.0, q.t);
+    }
+  }
+  for (int k = 0; k < K; ++k)
+    if (!slots[k]->done) finish(*slots[k], k);
+  CC_CUDA(cudaStreamSynchronize(ex.stream));
+  return CC_OK;
 }
 
 }  // namespace ccpnk
