@@ -29,8 +29,9 @@ def solve(name: str, tol: float = 1e-10, maxiter: int = 400):
     f, Bc, _ = cc.to_eigenbasis(s.fock, s.B, s.o)
     t0 = time.time()
     t1, t2, e, hist = cc.solve_fp_diis(f, Bc, s.o, tol=tol, maxiter=maxiter, diis_size=12)
+    to_1e8 = next((i + 1 for i, r in enumerate(hist) if r < 1e-8), None)
     return {"o": s.o, "v": s.v, "naux": s.naux, "e_corr": e, "res_norm": hist[-1],
-            "iterations": len(hist), "seconds": round(time.time() - t0, 1),
+            "iterations": len(hist), "iterations_to_1e-8": to_1e8, "seconds": round(time.time() - t0, 1),
             "solver": "oracle fp+diis(12), eigenbasis, generalised MP2 start"}
 
 
