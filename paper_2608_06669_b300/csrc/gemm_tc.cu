@@ -192,15 +192,16 @@ __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
 //   x_k = sign(x_k) sum_{s=1..S} d_s(x_k) 2^(sigma - OZ_BETA s) + (error < 2^(sigma - OZ_BETA S)),
 // with sigma the row's exponent (|x_k| < 2^sigma) and integer digits 0 <= d_s < 2^OZ_BETA, which
 // BF16 holds exactly. A product of two digit slices is then a sum of integers: each MMA chunk of
-// at most OZ_NK k blocks sums at most OZ_NK * 64 products below 2^(2 OZ_BETA), under 2^22, which
-// the FP32 accumulator represents exactly. The slice products of one level L = s + t share the
+// at most nk k blocks sums at most nk * 64 products below 2^(2 OZ_BETA), an integer below 2^22
+// for the default nk = 16 (below 2^24 up to nk = 64), which the FP32 accumulator represents
+// exactly. The slice products of one level L = s + t share the
 // scale 2^(sigma_i + tau_j - OZ_BETA L); levels up to S + 1 are kept (the first term dropped is
 // below 2^(-OZ_BETA S) of the leading one) and added in 64-bit integer fixed point, so the only
 // rounding is the final conversion to FP64.
 // ---------------------------------------------------------------------------
 constexpr int OZ_S = 8;      // slices per operand: 48 significant bits
 constexpr int OZ_BETA = 6;   // bits per slice digit
-constexpr int OZ_NK = 16;    // k blocks (of 64) per exact FP32 chunk: 16 * 64 * 63^2 < 2^22
+constexpr int OZ_NK = 16;    // default k blocks (of 64) per exact FP32 chunk: 16 * 64 * 63^2 < 2^22
 
 // Pass 1 of the digit staging: the largest biased exponent of every staged row (a row of A or
 // a column of B), one warp per piece of ROW_PIECE elements of a row, combined by an integer
@@ -285,11 +286,68 @@ __global__ void oz_digits_kernel(const double* __restrict__ src, CIdx rix, CIdx 
   }
 }
 
+// Both passes in one kernel for rows of at most a few thousand elements: one warp per staged
+// row finds the row's exponent (warp maximum, no atomics) and then writes its digits (the second
+// read of the row comes from L1/L2). Writes emax like the two-pass version.
+__global__ void oz_stage_rows_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
+                                     int batch, int rows_pad, int k_pad, int rev, unsigned* __restrict__ emax,
+                                     __nv_bfloat16* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const long long items = (long long)batch * rows_pad;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const size_t row_len = (size_t)OZ_S * k_pad;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  for (long long q = w0; q < items; q += nw) {
+    const int b = (int)(q / rows_pad), r = (int)(q - (long long)b * rows_pad);
+    __nv_bfloat16* row = out + (size_t)q * row_len;
+    if (r >= rows) {
+      for (size_t k = lane; k < row_len; k += 32) row[k] = zero;
+      if (lane == 0) emax[q] = 0;
+      continue;
+    }
+    const double* srow = src + cidx(bix, b) + cidx(rix, r);
+    unsigned e = 0;
+    CWalk kw;
+    kw.init(kix, lane);
+    for (int k = lane; k < K; k += 32) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
+      e = max(e, (unsigned)((bits >> 52) & 0x7FF));
+      kw.step(kix, 32);
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (lane == 0) emax[q] = e;
+    const unsigned em = max(e, 1u);
+    kw.init(kix, lane);
+    for (int k = lane; k < k_pad; k += 32) {
+      unsigned long long qv = 0, neg = 0;
+      if (k < K) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
+        unsigned ex = (unsigned)((bits >> 52) & 0x7FF);
+        unsigned long long m = bits & ((1ull << 52) - 1);
+        if (ex) m |= 1ull << 52;
+        else ex = 1;
+        neg = bits >> 63;
+        const unsigned sh = em - ex + 53 - OZ_BETA * OZ_S;
+        qv = sh >= 64 ? 0ull : (m >> sh);
+      }
+#pragma unroll
+      for (int sl = 1; sl <= OZ_S; ++sl) {
+        const int d = (int)((qv >> (OZ_BETA * (OZ_S - sl))) & ((1u << OZ_BETA) - 1));
+        const float f = neg ? -(float)d : (float)d;
+        const int seg = rev ? OZ_S - sl : sl - 1;
+        row[(size_t)seg * k_pad + k] = __float2bfloat16_rn(f);
+      }
+      kw.step(kix, 32);
+    }
+  }
+}
+
 // C = alpha * sum over levels of the exact chunk sums (scaled per level) + beta * C. One warp
 // per piece of an output row; the chunk sums are integers below 2^22, added per level in int64
 // and combined in 64-bit fixed point with the levels' scales 2^(OZ_BETA (S + 1 - L) - gsh)
 // (gsh > 0 drops low bits of the smallest levels so that the sum stays below 2^62).
-__global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, int kseg, int gsh,
+__global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, int kseg, int nk, int gsh,
                                   const unsigned* __restrict__ expA, int rowsA_pad, const unsigned* __restrict__ expB,
                                   int rowsB_pad, int piece) {
   const int lane = threadIdx.x & 31;
@@ -311,7 +369,7 @@ __global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, in
       long long acc = 0;
       int v = 0;
       for (int L = 2; L <= OZ_S + 1; ++L) {
-        const int nch = ((L - 1) * kseg + OZ_NK - 1) / OZ_NK;
+        const int nch = ((L - 1) * kseg + nk - 1) / nk;
         long long lv = 0;
         for (int c = 0; c < nch; ++c, ++v) lv += (long long)__float2int_rn(pr[(size_t)v * tot + n]);
         const int sh = OZ_BETA * (OZ_S + 1 - L) - gsh;
@@ -996,9 +1054,9 @@ void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>
 // as OZ_S BF16 digit slices with per-row exponents, run every (level, chunk) slice product as a
 // split of one persistent kind::f16 launch writing exact FP32 partial sums, and combine them in
 // integer fixed point into C = alpha A B + beta C.
-int oz_splits(int kseg) {
+int oz_splits(int kseg, int nk) {
   int n = 0;
-  for (int L = 2; L <= OZ_S + 1; ++L) n += ((L - 1) * kseg + OZ_NK - 1) / OZ_NK;
+  for (int L = 2; L <= OZ_S + 1; ++L) n += ((L - 1) * kseg + nk - 1) / nk;
   return n;
 }
 
@@ -1007,7 +1065,8 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
   const int k_pad = (g.K + TK - 1) / TK * TK;
   const int kseg = k_pad / TK, kk = OZ_S * k_pad;
-  const int nsplit = oz_splits(kseg);
+  const int nk = std::max(1, std::min(64, ex.emu_chunk));
+  const int nsplit = oz_splits(kseg, nk);
   auto blocks_for_rows = [&](size_t rows) {
     return (int)std::max<size_t>(1, std::min<size_t>((rows + 7) / 8, (size_t)ex.sm_count * 16));
   };
@@ -1020,10 +1079,15 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   auto* fB = reinterpret_cast<__nv_bfloat16*>(stB.p);
   auto* eA = reinterpret_cast<unsigned*>(exA.p);
   auto* eB = reinterpret_cast<unsigned*>(exB.p);
-  CC_CUDA(cudaMemsetAsync(eA, 0, (size_t)g.batch * rowsA * sizeof(unsigned), ex.stream));
-  CC_CUDA(cudaMemsetAsync(eB, 0, (size_t)g.batch * rowsB * sizeof(unsigned), ex.stream));
   auto stage = [&](const double* src, const CIdx& rix, const CIdx& kix, const CIdx& bix, int rows, int rows_pad,
                    int rev, unsigned* e, __nv_bfloat16* f) {
+    if (g.K <= 2048) {  // short rows: one warp per row, both passes in one kernel
+      oz_stage_rows_kernel<<<blocks_for_rows((size_t)g.batch * rows_pad), 256, 0, ex.stream>>>(
+          src, rix, kix, bix, rows, g.K, g.batch, rows_pad, k_pad, rev, e, f);
+      ex.count();
+      return;
+    }
+    CC_CUDA(cudaMemsetAsync(e, 0, (size_t)g.batch * rows_pad * sizeof(unsigned), ex.stream));
     const size_t pieces1 = (size_t)g.batch * rows * ((g.K + ROW_PIECE - 1) / ROW_PIECE);
     oz_rowexp_kernel<<<blocks_for_rows(pieces1), 256, 0, ex.stream>>>(src, rix, kix, bix, rows, g.K, g.batch,
                                                                         rows_pad, e);
@@ -1047,10 +1111,10 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   a.batch = g.batch;
   a.m_fast = a.num_m <= a.num_n ? 1 : 0;
   a.splits = nsplit;
-  a.kchunk = OZ_NK;
+  a.kchunk = nk;
   a.oz_S = OZ_S;
   a.oz_kseg = kseg;
-  a.oz_nk = OZ_NK;
+  a.oz_nk = nk;
   const long long tiles = (long long)a.num_m * a.num_n * g.batch * nsplit;
   CC_REQUIRE(tiles < (1LL << 31), CC_ERR_INVALID, "FP64-emulated contraction: too many tiles");
   a.tiles = (int)tiles;
@@ -1082,7 +1146,7 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
   const size_t items = rows * ((g.N + piece - 1) / piece);
   const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
-  oz_combine_kernel<<<rblocks, 256, 0, ex.stream>>>(g, a.part, kseg, gsh, eA, rowsA, eB, rowsB, piece);
+  oz_combine_kernel<<<rblocks, 256, 0, ex.stream>>>(g, a.part, kseg, nk, gsh, eA, rowsA, eB, rowsB, piece);
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);

@@ -22,6 +22,7 @@ struct cc_ctx {
   unsigned long long wait_ns = 4000000000ull;  // CC_OPT_WAIT_LIMIT_NS
   long long stage_cap = -1;                    // CC_OPT_STAGE_CACHE_BYTES (-1: the default)
   int graphs = 1;                              // CC_OPT_GRAPHS
+  int emu_chunk = 16;                          // CC_OPT_EMU_CHUNK
   ccpnk::Exec ex() {
     ccpnk::Exec e;
     e.stream = stream;
@@ -33,6 +34,7 @@ struct cc_ctx {
     e.wait_ns = wait_ns;
     e.stage_cap = stage_cap;
     e.graphs = graphs;
+    e.emu_chunk = emu_chunk;
     return e;
   }
 };

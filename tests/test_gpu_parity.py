@@ -328,13 +328,20 @@ def test_fp64_emulated_residual_and_jvp_parity(ctx, o, v, naux, gauge):
     assert np.abs(j1 - p1).max() <= TOL64 * scale and np.abs(j2 - p2).max() <= TOL64 * scale
 
 
-def test_fp64_emulated_workload_residual(ctx):
+@pytest.mark.parametrize("chunk", [16, 64, 1])
+def test_fp64_emulated_workload_residual(ctx, chunk):
+    """The o=10 v=90 workload; the exact chunks of the emulation summing 16 (default), 64 (sums
+    up to just below 2^24) or 1 k block of 64 products each."""
     s = synth.workload("o10v90_rotated")
     o, v = s.o, s.v
     t1, t2 = cc.mp2_guess(s.fock, s.B, o)
     p1, p2 = synth.random_amplitudes(np.random.default_rng(3), o, v, 0.01, 0.01)
     t1, t2 = t1 + p1, t2 + p2
-    r1, r2, e = gpu_system(ctx, s).residual(t1, t2, prec="fp64emu")
+    ctx.set_option("emu_chunk", chunk)
+    try:
+        r1, r2, e = gpu_system(ctx, s).residual(t1, t2, prec="fp64emu")
+    finally:
+        ctx.set_option("emu_chunk", 16)
     q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
     scale = max(np.abs(q1).max(), np.abs(q2).max())
     assert np.abs(r1 - q1).max() <= TOL64 * scale and np.abs(r2 - q2).max() <= TOL64 * scale
