@@ -132,8 +132,9 @@ const char* cc_last_error(const cc_ctx* ctx);
  *   tangent program (captured during the solve, released when it returns; the kernel timer, when
  *   on, keeps them eager); 0 launches every kernel. Results are the same bits either way.
  * CC_OPT_EMU_CHUNK: k blocks of 64 products that one exact FP32 chunk of CC_FP64_EMU sums
- *   (1..64, default 16: the chunk sums stay below 2^22; up to 64 they stay below 2^24, where
- *   FP32 still holds every integer exactly). Fewer, longer chunks move fewer partial sums.
+ *   (1..64, default 64: a chunk sum stays below 2^24, where FP32 still holds every integer
+ *   exactly). Results do not depend on it (the chunk sums are exact); fewer, longer chunks move
+ *   fewer partial sums.
  * Returns CC_OK or CC_ERR_INVALID (unknown option, value out of range). */
 #define CC_OPT_STAGE_CACHE_BYTES 1
 #define CC_OPT_WAIT_LIMIT_NS 2

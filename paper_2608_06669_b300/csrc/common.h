@@ -125,7 +125,7 @@ struct Exec {
   unsigned long long wait_ns = 4000000000ull;  // bound on every device-side wait (global timer)
   long long stage_cap = -1;                    // bytes of kept staged operands (-1: the default)
   int graphs = 1;                              // replay the JVPs of a solve from CUDA graphs
-  int emu_chunk = 16;                          // k blocks of 64 per exact chunk of the FP64 emulation
+  int emu_chunk = 64;                          // k blocks of 64 per exact chunk of the FP64 emulation
   void count(uint64_t k = 1) const {
     if (launches) *launches += k;
   }

@@ -201,7 +201,7 @@ __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
 // ---------------------------------------------------------------------------
 constexpr int OZ_S = 8;      // slices per operand: 48 significant bits
 constexpr int OZ_BETA = 6;   // bits per slice digit
-constexpr int OZ_NK = 16;    // default k blocks (of 64) per exact FP32 chunk: 16 * 64 * 63^2 < 2^22
+constexpr int OZ_NK = 64;    // default k blocks (of 64) per exact FP32 chunk: 64 * 64 * 63^2 < 2^24
 
 // Pass 1 of the digit staging: the largest biased exponent of every staged row (a row of A or
 // a column of B), one warp per piece of ROW_PIECE elements of a row, combined by an integer
@@ -343,6 +343,12 @@ __global__ void oz_stage_rows_kernel(const double* __restrict__ src, CIdx rix, C
   }
 }
 
+// 2^e as a double from its exponent bits (callers keep e inside the normal range)
+__device__ __forceinline__ double pow2(int e) {
+  e = max(-1022, min(1023, e));
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
 // C = alpha * sum over levels of the exact chunk sums (scaled per level) + beta * C. One warp
 // per piece of an output row; the chunk sums are integers below 2^22, added per level in int64
 // and combined in 64-bit fixed point with the levels' scales 2^(OZ_BETA (S + 1 - L) - gsh)
@@ -363,6 +369,10 @@ __global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, in
     const long long rowoff = cidx(g.cb, b) + cidx(g.cm, m);
     const float* pr = part + (size_t)qrow * g.N;
     const int ea = (int)max(expA[(size_t)b * rowsA_pad + m], 1u) - 1022;  // sigma of row m
+    // alpha 2^(sigma_m - beta (S + 1) + gsh) for the row, 2^tau_n per column: the scaling is two
+    // multiplications by exact powers of two while their exponents are inside the normal range
+    const int er = ea - OZ_BETA * (OZ_S + 1) + gsh;
+    const double row_scale = g.alpha * pow2(er);
     CWalk cw;
     cw.init(g.cn, n0 + lane);
     for (int n = n0 + lane; n < n1; n += 32) {
@@ -376,8 +386,9 @@ __global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, in
         acc += sh >= 0 ? (lv << sh) : ((lv + (1ll << (-sh - 1))) >> (-sh));
       }
       const int eb = (int)max(expB[(size_t)b * rowsB_pad + n], 1u) - 1022;
-      const int e = ea + eb - OZ_BETA * (OZ_S + 1) + gsh;
-      const double val = g.alpha * ldexp((double)acc, e);
+      const double val = (er > -960 && er < 960 && eb > -960 && eb < 960 && er + eb > -960 && er + eb < 960)
+                             ? (double)acc * row_scale * pow2(eb)
+                             : g.alpha * ldexp((double)acc, er + eb);
       double* c = g.C + rowoff + cw.off;
       *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
       cw.step(g.cn, 32);

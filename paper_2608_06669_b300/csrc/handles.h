@@ -22,7 +22,7 @@ struct cc_ctx {
   unsigned long long wait_ns = 4000000000ull;  // CC_OPT_WAIT_LIMIT_NS
   long long stage_cap = -1;                    // CC_OPT_STAGE_CACHE_BYTES (-1: the default)
   int graphs = 1;                              // CC_OPT_GRAPHS
-  int emu_chunk = 16;                          // CC_OPT_EMU_CHUNK
+  int emu_chunk = 64;                          // CC_OPT_EMU_CHUNK
   ccpnk::Exec ex() {
     ccpnk::Exec e;
     e.stream = stream;

@@ -330,8 +330,8 @@ def test_fp64_emulated_residual_and_jvp_parity(ctx, o, v, naux, gauge):
 
 @pytest.mark.parametrize("chunk", [16, 64, 1])
 def test_fp64_emulated_workload_residual(ctx, chunk):
-    """The o=10 v=90 workload; the exact chunks of the emulation summing 16 (default), 64 (sums
-    up to just below 2^24) or 1 k block of 64 products each."""
+    """The o=10 v=90 workload; the exact chunks of the emulation summing 64 (the default: sums up
+    to just below 2^24), 16 or 1 k block of 64 products each."""
     s = synth.workload("o10v90_rotated")
     o, v = s.o, s.v
     t1, t2 = cc.mp2_guess(s.fock, s.B, o)
@@ -341,7 +341,7 @@ def test_fp64_emulated_workload_residual(ctx, chunk):
     try:
         r1, r2, e = gpu_system(ctx, s).residual(t1, t2, prec="fp64emu")
     finally:
-        ctx.set_option("emu_chunk", 16)
+        ctx.set_option("emu_chunk", 64)
     q1, q2, eq = cc.residual(s.fock, s.B, o, t1, t2)
     scale = max(np.abs(q1).max(), np.abs(q2).max())
     assert np.abs(r1 - q1).max() <= TOL64 * scale and np.abs(r2 - q2).max() <= TOL64 * scale
@@ -362,3 +362,30 @@ def test_pnk_with_emulated_outer_residual(ctx, prec):
             q1, q2, eq = cc.residual(s.fock, s.B, s.o, t1, t2)
             assert np.sqrt((q1 ** 2).sum() + (q2 ** 2).sum()) < 1e-8 and abs(eq - rep["energy"]) < 1e-10
 
+
+
+@pytest.mark.parametrize("chunk", [16, 64])
+def test_fp64_emulation_chunk_sums_at_their_bound(ctx, chunk):
+    """Worst case for the exactness of the emulation's FP32 chunk sums: every entry of B is
+    1 - 2^-48, so every digit slice of the ladder build's operands holds the largest digit (63)
+    and a chunk of 64 (or 16) k blocks sums 4096 (1024) products 63 * 63 = 16,257,024 (4,064,256),
+    just below 2^24 (2^22). The emulated residual must still equal the native FP64 one."""
+    from paper_2608_06669_b300 import ccpnk
+
+    o, v, naux = 1, 40, 640
+    n = o + v
+    fock = np.diag(np.concatenate([[-1.0], np.linspace(0.5, 2.0, v)]))
+    B = np.full((naux, n, n), 1.0 - 2.0 ** -48)
+    g = ccpnk.System(ctx, o, v, naux, fock, B)
+    # t1 = 0 leaves the dressed factor equal to B, so the ladder build's operands keep the digits
+    _, t2 = synth.random_amplitudes(np.random.default_rng(5), o, v, 0.01, 0.01)
+    t1 = np.zeros((o, v))
+    ctx.set_option("emu_chunk", chunk)
+    try:
+        e1, e2, ee = g.residual(t1, t2, prec="fp64emu")
+    finally:
+        ctx.set_option("emu_chunk", 64)
+    f1, f2, ef = g.residual(t1, t2, prec="fp64")
+    scale = max(np.abs(f1).max(), np.abs(f2).max())
+    assert max(np.abs(e1 - f1).max(), np.abs(e2 - f2).max()) <= 1e-12 * scale
+    assert abs(ee - ef) <= 1e-12 * max(1.0, abs(ef))
