@@ -257,6 +257,13 @@ def roofline_entry(rec, kind, peaks, peak_kind):
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches": n,
                 "ms_per_launch": ms / n, "flops_per_launch": 3.0 * fl / n, "logical_tflops": fl / (ms / 1e3) / 1e12,
                 "peak_source": f"{peak_kind} bf16 burst x 1.1/2.25 (of {peak_kind})"}
+    if kind == "bf16x3":
+        peak = peaks["bf16_tflops"]
+        ach = 3.0 * fl / (ms / 1e3) / 1e12
+        return {"bound": "tensor", "kernel": "gemm_tc_kernel<bf16> (ladder build of the JVP, three BF16 passes)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches": n,
+                "ms_per_launch": ms / n, "flops_per_launch": 3.0 * fl / n, "logical_tflops": fl / (ms / 1e3) / 1e12,
+                "peak_source": f"{peak_kind} bf16 burst (of {peak_kind})"}
     peak = peaks["bf16_tflops"]
     ach = 36.0 * fl / (ms / 1e3) / 1e12
     return {"bound": "tensor", "kernel": "FP64-emulated ladder build: oz_rowexp/oz_digits staging, "
@@ -332,7 +339,7 @@ def large_block(args, peaks, peak_kind):
     return out
 
 
-def serve_pass(reqs, prec, extra, args, slots=None, group=1):
+def serve_pass(reqs, prec, extra, args, slots=None, group=1, policy="fifo"):
     """Submits the requests at their arrival times to a fresh server and waits for all of them;
     returns p50/p99 time to solution, solves/s and convergence. group > 1: grouped mode (a slot
     solves up to that many compatible requests together, in lockstep)."""
@@ -343,6 +350,7 @@ def serve_pass(reqs, prec, extra, args, slots=None, group=1):
     srv = ccpnk.Server(0, mem_budget=200 << 30, max_slots=slots or args.slots)
     if group > 1:
         srv.set_grouping(group)
+    srv.set_policy(policy)
     t_start = time.perf_counter()
     tickets = []
     for arrival, sy in reqs:
@@ -365,7 +373,7 @@ def serve_pass(reqs, prec, extra, args, slots=None, group=1):
     lat = np.array([f - sub for sub, _, f in times])
     span = max(f for _, _, f in times) - min(sub for sub, _, _ in times)
     conv = [results[t][2]["status_code"] == 0 for t in tickets]
-    return {"requests": len(reqs), "slots": slots or args.slots, "group": group,
+    return {"requests": len(reqs), "slots": slots or args.slots, "group": group, "policy": policy,
             "solves_per_s": len(tickets) / span, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(conv)), "makespan_s": span,
             "max_concurrent": stats["max_running"],
@@ -385,14 +393,17 @@ def served_block(args):
     reqs = synth.served_requests(args.serve_default)
     out = {"slots": args.slots, "arrivals": "exponential, mean 20 ms", "caps": {
         "max_newton": args.max_newton, "max_seconds": args.solve_seconds}}
-    out["mixed"] = serve_pass(reqs, "tf32x3", {"outer_prec": 5}, args)
+    mixed = {"outer_prec": 5}
+    out["mixed"] = serve_pass(reqs, args.prec, mixed, args)
+    # shortest first: a free slot takes the waiting request with the least estimated work
+    out["mixed_shortest_first"] = serve_pass(reqs, args.prec, mixed, args, policy="shortest_first")
     # grouped mode: fewer slots, each solving up to --serve-group requests in one lockstep batch
-    out["mixed_grouped"] = serve_pass(reqs, "tf32x3", {"outer_prec": 5}, args, slots=args.group_slots,
-                                      group=args.serve_group)
+    out["mixed_grouped"] = serve_pass(reqs, args.prec, mixed, args, slots=args.group_slots,
+                                      group=args.serve_group, policy="shortest_first")
     sub = reqs if args.serve_fp64_all else [(t, sy) for t, sy in reqs if sy.o <= args.serve_fp64_max_o]
     out["subset"] = ("all" if args.serve_fp64_all else f"the {len(sub)} requests with o <= {args.serve_fp64_max_o}")
     out["fp64_on_subset"] = serve_pass(sub, "fp64", {}, args)
-    out["mixed_on_subset"] = serve_pass(sub, "tf32x3", {"outer_prec": 5}, args)
+    out["mixed_on_subset"] = serve_pass(sub, args.prec, mixed, args)
     return out
 
 
@@ -428,7 +439,7 @@ def run_ours(args):
         g.solve(**kw)
     torch.cuda.synchronize()
 
-    launches0 = ctx.launches
+    launches0, calls0 = ctx.launches, ctx.launch_calls
     times, reports = [], []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -443,6 +454,7 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1) / 1e3)
             reports.append(rep)
     launches = ctx.launches - launches0
+    calls = ctx.launch_calls - calls0
     # the kernel timer brackets the ladder GEMMs with events, which keeps the JVPs eager (no
     # CUDA graphs), so it runs on repeats of the timed solve right after the timed region
     ctx.profile(True)
@@ -451,7 +463,7 @@ def run_ours(args):
         dt, _ = timed(lambda: g.solve(**kw))
         t_prof += dt
     tags = {"fp64": ctx.profile_get("ladder_build.fp64"), "emu": ctx.profile_get("ladder_build.emu"),
-            "tf32x3": ctx.profile_get("ladder_build.tf32")}
+            "tf32x3": ctx.profile_get("ladder_build.tf32"), "bf16x3": ctx.profile_get("ladder_build.bf16")}
     ctx.profile(False)
     t_mean = statistics.mean(times)
     t_max = t_mean
@@ -468,7 +480,7 @@ def run_ours(args):
         "fp64_pnk": dict(method="pnk", prec="fp64", af_direct=1),
         "fp64emu_pnk": dict(method="pnk", prec="fp64emu", af_direct=1, outer_prec=5),
         "mixed_pnk_af_gmres": dict(method="pnk", prec=args.prec, af_direct=0, outer_prec=args.outer),
-        "mixed_pnk_bf16x3": dict(method="pnk", prec="bf16x3", af_direct=1, outer_prec=args.outer),
+        "mixed_pnk_tf32x3": dict(method="pnk", prec="tf32x3", af_direct=1, outer_prec=args.outer),
         "mixed_pnk_df64_outer": dict(method="pnk", prec=args.prec, af_direct=1, outer_prec=4),
         "df64_pnk": dict(method="pnk", prec="df64", af_direct=1, outer_prec=4),
     }
@@ -527,6 +539,7 @@ def run_ours(args):
         "e2e": {"value": statistics.mean(e2e_times) if e2e_times else None, "unit": "s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // max(args.steps, 1),
+        "host_launch_calls": calls // max(args.steps, 1),
         "clocks": clk.summary(),
         "fp64_pnk_s": var_out["fp64_pnk"]["s"] if var_out else None,
         "speedup_mixed_vs_fp64": var_out["fp64_pnk"]["s"] / t_max if var_out else None,
@@ -800,7 +813,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "bf16x3", "tf32", "fp64", "fp64emu"])
+    ap.add_argument("--prec", default="bf16x3", choices=["tf32x3", "bf16x3", "tf32", "fp64", "fp64emu"])
     ap.add_argument("--outer", type=int, default=5, help="outer-residual precision code (0 FP64, 4 DF64, 5 FP64-emulated)")
     ap.add_argument("--no-large", action="store_true", help="skip the o=30 v=270 block of the main line")
     ap.add_argument("--no-fp64-large", action="store_true", help="skip the native FP64 residual/JVP at o=30 v=270")

@@ -153,8 +153,12 @@ int cc_ctx_selftest_wait(cc_ctx* ctx);
 int cc_probe_fma_rate(int device, int fp64, double* tflops);
 /* Device bytes currently held by the context's pools. */
 size_t cc_ctx_device_bytes(const cc_ctx* ctx);
-/* Number of kernel launches the context has issued since it was created. */
+/* Number of kernels the context has run since it was created (a replayed CUDA graph counts
+ * its kernel nodes). */
 uint64_t cc_ctx_launches(const cc_ctx* ctx);
+/* Number of host launch calls the context has made: one per kernel launch and one per CUDA
+ * graph replay. */
+uint64_t cc_ctx_launch_calls(const cc_ctx* ctx);
 /* Kernel timer (tracing): enable != 0 clears the records and brackets GEMM launches with CUDA
  * events on the context's stream; enable = 0 turns it off. enable = 1 times the two GEMMs of
  * the particle-particle ladder, tagged "ladder_build.<p>" and "ladder_contract.<p>" (<p> =
@@ -256,6 +260,14 @@ int cc_energy_noalloc(const cc_sys* sys, const double* t1, const double* t2, dou
  * device-memory estimate fits under mem_budget (0: no budget), so the kernels of different
  * requests overlap on the device. Results are bitwise independent of what else runs. */
 int cc_server_create(cc_server** srv, int device, size_t mem_budget, int max_slots);
+/* Admission order: CC_SERVE_FIFO (default) takes the oldest waiting request; with
+ * CC_SERVE_SHORTEST_FIRST a free slot takes the waiting request with the least estimated work
+ * ((naux + o^2) v^4, the residual's ladder cost) divided by (1 + seconds it has waited), so small
+ * requests do not queue behind large ones and a large one is not passed over for ever. Results
+ * do not depend on the order. CC_ERR_INVALID for another value. */
+#define CC_SERVE_FIFO 0
+#define CC_SERVE_SHORTEST_FIRST 1
+int cc_server_set_policy(cc_server* srv, int policy);
 /* Grouped mode: with group_max > 1 a slot that takes a waiting request also takes up to
  * group_max - 1 later waiting requests with identical NK/PNK options whose memory estimates fit,
  * and solves them as one lockstep batch (cc_solve_batch: the same contraction of every request in

@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
             "cc_last_error": (ctypes.c_char_p, [vp]),
             "cc_ctx_device_bytes": (sz, [vp]),
             "cc_ctx_launches": (u64, [vp]),
+            "cc_ctx_launch_calls": (u64, [vp]),
             "cc_ctx_set_option": (i, [vp, i, ctypes.c_longlong]),
             "cc_ctx_selftest_wait": (i, [vp]),
             "cc_probe_fma_rate": (i, [i, i, ctypes.POINTER(d)]),
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "cc_serve_poll": (i, [vp, u64, ctypes.POINTER(Report), vp, vp]),
             "cc_serve_cancel": (i, [vp, u64]),
             "cc_server_set_grouping": (i, [vp, i]),
+            "cc_server_set_policy": (i, [vp, i]),
             "cc_serve_times": (i, [vp, u64, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
             "cc_server_stats": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)]),
         }
@@ -175,6 +177,10 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().cc_ctx_launches(self.h))
+
+    @property
+    def launch_calls(self) -> int:
+        return int(lib().cc_ctx_launch_calls(self.h))
 
     def set_option(self, name: str, value: int):
         """cc_ctx_set_option: 'stage_cache_bytes' (-1 default, 0 off), 'wait_limit_ns' or 'graphs' (0/1)."""
@@ -370,6 +376,12 @@ class Server:
         st = lib().cc_server_set_grouping(self.h, int(group_max))
         if st < 0:
             raise CCError(st, "cc_server_set_grouping failed")
+
+    def set_policy(self, policy: str):
+        """cc_server_set_policy: 'fifo' or 'shortest_first'."""
+        st = lib().cc_server_set_policy(self.h, {"fifo": 0, "shortest_first": 1}[policy])
+        if st < 0:
+            raise CCError(st, "cc_server_set_policy failed")
 
     def cancel(self, ticket: int) -> int:
         """cc_serve_cancel: drops a waiting request or stops a running one."""

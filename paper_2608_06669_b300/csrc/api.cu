@@ -286,6 +286,8 @@ size_t cc_ctx_device_bytes(const cc_ctx* ctx) { return ctx && ctx->pool ? ctx->p
 
 uint64_t cc_ctx_launches(const cc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+uint64_t cc_ctx_launch_calls(const cc_ctx* ctx) { return ctx ? ctx->launch_calls : 0; }
+
 int cc_ctx_set_option(cc_ctx* ctx, int option, long long value) {
   if (!ctx) return CC_ERR_INVALID;
   return guarded(ctx, [&]() {

@@ -559,10 +559,11 @@ void Engine::tangent(const double* d, double* jd, cc_precision prec) {
 void Engine::capture(TanGraph& G, cc_precision prec) {
   if (!cap_stream_) CC_CUDA(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
   const Exec saved = ex_;
-  uint64_t nodes = 0;
+  uint64_t nodes = 0, calls = 0;
   std::vector<void*> rec;
   ex_.stream = cap_stream_;  // captured on a private stream, launched on the context's
   ex_.launches = &nodes;
+  ex_.calls = &calls;
   ex_.pool->record = &rec;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeRelaxed);

@@ -118,7 +118,8 @@ struct Prof {
 struct Exec {
   cudaStream_t stream = nullptr;
   Pool* pool = nullptr;
-  uint64_t* launches = nullptr;  // incremented for every kernel launch
+  uint64_t* launches = nullptr;  // kernels run: one per launch, a graph's kernel nodes per replay
+  uint64_t* calls = nullptr;     // host launch calls: one per kernel launch or graph replay
   int* dev_flag = nullptr;       // device error flag (bounded waits, bad shapes)
   int sm_count = 148;
   Prof* prof = nullptr;
@@ -128,6 +129,7 @@ struct Exec {
   int emu_chunk = 64;                          // k blocks of 64 per exact chunk of the FP64 emulation
   void count(uint64_t k = 1) const {
     if (launches) *launches += k;
+    if (calls) *calls += 1;
   }
   // brackets a launch with events when the timer is on and the launch is tagged
   bool timing(const char* tag) const { return prof && prof->on && tag; }

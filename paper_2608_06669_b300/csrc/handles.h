@@ -15,6 +15,7 @@ struct cc_ctx {
   bool own_stream = false;
   std::unique_ptr<ccpnk::Pool> pool;
   uint64_t launches = 0;
+  uint64_t launch_calls = 0;
   int sm_count = 148;
   int* dflag = nullptr;  // device error flag written by bounded waits
   std::string err;
@@ -28,6 +29,7 @@ struct cc_ctx {
     e.stream = stream;
     e.pool = pool.get();
     e.launches = &launches;
+    e.calls = &launch_calls;
     e.sm_count = sm_count;
     e.dev_flag = dflag;
     e.prof = &prof;

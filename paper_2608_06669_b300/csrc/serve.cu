@@ -28,6 +28,7 @@ struct Request {
   std::vector<double> fock, B;  // host copies taken at submit
   cc_solve_opts opts{};
   size_t footprint = 0;  // admission estimate (bytes)
+  double cost = 0;       // work estimate of one residual evaluation ((naux + o^2) v^4)
   // results
   bool done = false, released = false;
   int status = CC_PENDING;
@@ -76,11 +77,30 @@ struct cc_server {
   int running = 0, max_running = 0;
   bool stop = false;
   int group_max = 1;  // > 1: a slot solves up to this many compatible requests together
+  int policy = CC_SERVE_FIFO;
   std::vector<std::thread> workers;
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
 
 namespace {
+
+// The waiting request a free slot takes next (called with the lock held, queue not empty):
+// the oldest (FIFO), or the one with the least work, its estimate divided by (1 + seconds
+// waited) so that a large request is not passed over for ever (shortest first).
+std::deque<Request*>::iterator next_request(cc_server* srv) {
+  if (srv->policy != CC_SERVE_SHORTEST_FIRST) return srv->queue.begin();
+  const double now = srv->now();
+  auto best = srv->queue.begin();
+  double bv = 1e300;
+  for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it) {
+    const double v = (*it)->cost / (1.0 + std::max(0.0, now - (*it)->t_submit));
+    if (v < bv) {
+      bv = v;
+      best = it;
+    }
+  }
+  return best;
+}
 
 // Requests a slot may solve together: NK or PNK with identical options (so one lockstep batch
 // runs them all exactly as each would run alone).
@@ -120,16 +140,21 @@ void worker_main(cc_server* srv, int slot) {
     std::vector<Request*> batch;
     {
       std::unique_lock<std::mutex> lk(srv->mu);
-      // FIFO admission: the oldest request goes first once its memory estimate fits
+      // admission: the request the policy puts first goes once its memory estimate fits
       srv->cv.wait(lk, [&] {
         if (srv->stop) return true;
         if (srv->queue.empty()) return false;
-        Request* h = srv->queue.front();
+        Request* h = *next_request(srv);
         return srv->budget == 0 || srv->in_use + h->footprint <= srv->budget || srv->running == 0;
       });
       if (srv->stop) break;
-      batch.push_back(srv->queue.front());
-      srv->queue.pop_front();
+      auto head = next_request(srv);
+      batch.push_back(*head);
+      srv->queue.erase(head);
+      if (srv->policy == CC_SERVE_SHORTEST_FIRST)  // group the cheapest compatible ones with it
+        std::stable_sort(srv->queue.begin(), srv->queue.end(), [](const Request* a, const Request* b) {
+          return a->cost < b->cost;
+        });
       size_t fp = batch[0]->footprint;
       // grouped mode: later waiting requests that can run in the same lockstep batch and fit
       for (auto it = srv->queue.begin(); (int)batch.size() < srv->group_max && it != srv->queue.end();) {
@@ -265,6 +290,7 @@ int cc_serve_submit(cc_server* srv, int o, int v, int naux, const double* fock, 
   r->B.assign(B, B + (size_t)naux * n * n);
   r->opts = *opts;
   r->footprint = footprint_bytes(o, v, naux, *opts);
+  r->cost = ((double)naux + (double)o * o) * std::pow((double)v, 4.0);
   if (srv->budget && r->footprint > srv->budget) return CC_ERR_OOM;  // never admissible
   {
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -294,6 +320,13 @@ int cc_serve_poll(cc_server* srv, uint64_t ticket, cc_report* report, double* t1
   r->t2.clear();
   r->t2.shrink_to_fit();
   return r->status;
+}
+
+int cc_server_set_policy(cc_server* srv, int policy) {
+  if (!srv || (policy != CC_SERVE_FIFO && policy != CC_SERVE_SHORTEST_FIRST)) return CC_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->policy = policy;
+  return CC_OK;
 }
 
 int cc_server_set_grouping(cc_server* srv, int group_max) {

@@ -111,3 +111,19 @@ def test_fp64_residual_near_degenerate_workload(ctx):
         r1, r2, e = g.residual(t1, t2, prec=prec)
         assert nerr((r1, r2), (q1, q2)) <= TOL64, prec
         assert abs(e - eq) <= TOL64 * max(1.0, abs(eq))
+
+
+def test_spot_check_at_the_large_workload(ctx):
+    """The o=30 v=270 naux=900 workload, full size: two capped PNK steps (mixed JVPs, FP64-emulated
+    outer residual), then the oracle's residual and energy at the GPU's last iterate against the
+    GPU's own residual there, native FP64 and emulated, element by element. (The workload has
+    no root the reference solver reaches, so the check is made at the iterate.)"""
+    s = synth.workload("o30v270_rotated")
+    g = gsys(ctx, s)
+    t1, t2, rep = g.solve("pnk", "tf32x3", af_direct=1, outer_prec=5, max_outer=2)
+    assert rep["newton_iters"] == 2 and np.isfinite(rep["res_norm"])
+    q1, q2, eq = cc.residual(s.fock, s.B, s.o, t1, t2)
+    for prec in ("fp64emu", "fp64"):
+        r1, r2, e = g.residual(t1, t2, prec=prec)
+        assert nerr((r1, r2), (q1, q2)) <= TOL64, prec
+        assert abs(e - eq) <= TOL64 * max(1.0, abs(eq)), prec
