@@ -34,6 +34,7 @@ METRIC = "PNK time-to-‖R‖<1e-8, mixed vs FP64; residual TFLOP/s vs peak; p50
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # TF32 dense tensor peak: measured bf16 burst x the nominal TF32/BF16 ratio (1.1 / 2.25)
 TF32_RATIO = 1.1 / 2.25
+OZ_PRODUCTS = 45  # BF16 slice products per FP64-equivalent product of the emulation (9 slices)
 
 
 def rank_info():
@@ -240,7 +241,7 @@ def run_reference(args):
 
 def roofline_entry(rec, kind, peaks, peak_kind):
     """Roofline of one tagged GEMM from the kernel timer's (launches, ms, flops) record. kind:
-    'fp64' (FMA pipe), 'tf32x3' (three TF32 passes on tcgen05), 'emu' (Ozaki slices: 36 BF16
+    'fp64' (FMA pipe), 'tf32x3' (three TF32 passes on tcgen05), 'emu' (Ozaki slices: 45 BF16
     slice products per FP64-equivalent product on tcgen05 kind::f16)."""
     n, ms, fl = rec
     if not n or ms <= 0:
@@ -265,14 +266,15 @@ def roofline_entry(rec, kind, peaks, peak_kind):
                 "ms_per_launch": ms / n, "flops_per_launch": 3.0 * fl / n, "logical_tflops": fl / (ms / 1e3) / 1e12,
                 "peak_source": f"{peak_kind} bf16 burst (of {peak_kind})"}
     peak = peaks["bf16_tflops"]
-    ach = 36.0 * fl / (ms / 1e3) / 1e12
-    return {"bound": "tensor", "kernel": "FP64-emulated ladder build: oz_rowexp/oz_digits staging, "
-                                         "gemm_tc_kernel<bf16, partials>, oz_combine",
+    ach = OZ_PRODUCTS * fl / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "FP64-emulated ladder build: digit staging (oz_stage_rows or oz_rowexp + "
+                                         "oz_digits), then oz_gemm_kernel (slice products summed on chip) or "
+                                         "gemm_tc_kernel<bf16, partials> + oz_combine, by shape",
             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches": n,
-            "ms_per_launch": ms / n, "flops_per_launch": 36.0 * fl / n,
+            "ms_per_launch": ms / n, "flops_per_launch": OZ_PRODUCTS * fl / n,
             "fp64_equivalent_tflops": fl / (ms / 1e3) / 1e12,
-            "peak_source": f"{peak_kind} bf16 burst (of {peak_kind}); achieved counts the 36 BF16 slice products "
-                           f"of each FP64-equivalent product, time covers staging, MMA and the combine"}
+            "peak_source": f"{peak_kind} bf16 burst (of {peak_kind}); achieved counts the 45 BF16 slice products "
+                           f"of each FP64-equivalent product, time covers staging, MMA and the recombination"}
 
 
 def timed(fn):

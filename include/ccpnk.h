@@ -60,10 +60,12 @@ typedef enum {
                            products, two-sum accumulation; about 48 significant bits), for the
                            residual when FP64 FMA throughput is the limit */
   CC_FP64_EMU = 5       /* FP64-accurate contractions on the tensor cores: each FP64 row split into
-                           8 BF16 slices of 6-bit integer digits under a per-row exponent (Ozaki's
+                           9 BF16 slices of 6-bit integer digits under a per-row exponent (Ozaki's
                            error-free splitting), slice products summed exactly in FP32 chunks on
-                           tcgen05 kind::f16 and combined in 64-bit integer fixed point; 48
-                           significant bits per operand. Thin contractions stay on the FP64 pipe */
+                           tcgen05 kind::f16 and combined in 64-bit integer fixed point; every
+                           element rounded to nearest at 54 bits below its row's largest, so the
+                           representation errors carry no sign bias. Thin contractions stay on the
+                           FP64 pipe */
 } cc_precision;
 
 typedef enum {
@@ -132,14 +134,26 @@ const char* cc_last_error(const cc_ctx* ctx);
  *   tangent program (captured during the solve, released when it returns; the kernel timer, when
  *   on, keeps them eager); 0 launches every kernel. Results are the same bits either way.
  * CC_OPT_EMU_CHUNK: k blocks of 64 products that one exact FP32 chunk of CC_FP64_EMU sums
- *   (1..64, default 64: a chunk sum stays below 2^24, where FP32 still holds every integer
+ *   (1..64, default 64: a chunk sum stays within 2^24, where FP32 still holds every integer
  *   exactly). Results do not depend on it (the chunk sums are exact); fewer, longer chunks move
  *   fewer partial sums.
+ * CC_OPT_LADDER_PACK: the (c, d) split of the tensor-core particle-particle ladder: the slab
+ *   (ac|bd) goes through one more pass that forms its parts symmetric and antisymmetric under
+ *   c <-> d, and the contraction with the amplitudes runs over pairs i <= j, c <= d (half the
+ *   MMA work for an extra read and write of the slab). -1 (default) decides per shape by a time
+ *   model, 0 never, 1 always. Results agree within the precision's bound either way.
+ * CC_OPT_EMU_ONCHIP: how CC_FP64_EMU sums its slice products: 1 on chip (each 128 x 128 tile of
+ *   C runs all its slice products on one SM and adds the exact chunk sums in registers), 0
+ *   through FP32 partial sums in device memory and a combine pass (the slice products of one
+ *   tile spread over SMs), -1 (default) by a time model of the shape. The bits of the result
+ *   are the same either way.
  * Returns CC_OK or CC_ERR_INVALID (unknown option, value out of range). */
 #define CC_OPT_STAGE_CACHE_BYTES 1
 #define CC_OPT_WAIT_LIMIT_NS 2
 #define CC_OPT_GRAPHS 3
 #define CC_OPT_EMU_CHUNK 4
+#define CC_OPT_LADDER_PACK 5
+#define CC_OPT_EMU_ONCHIP 6
 int cc_ctx_set_option(cc_ctx* ctx, int option, long long value);
 /* Self-test of the bounded device waits: runs one kernel whose wait on an mbarrier that nothing
  * arrives at gives up after CC_OPT_WAIT_LIMIT_NS, so the call returns CC_ERR_TIMEOUT; the

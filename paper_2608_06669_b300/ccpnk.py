@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libccpnk.so")
 CC_OK, CC_PENDING = 0, 1
 STATUS = {-1: "CC_ERR_INVALID", -2: "CC_ERR_OOM", -3: "CC_ERR_NOT_CONVERGED", -4: "CC_ERR_DIVERGED",
           -5: "CC_ERR_CUDA", -6: "CC_ERR_TIMEOUT", -7: "CC_ERR_CANCELLED"}
-OPTION = {"stage_cache_bytes": 1, "wait_limit_ns": 2, "graphs": 3, "emu_chunk": 4}
+OPTION = {"stage_cache_bytes": 1, "wait_limit_ns": 2, "graphs": 3, "emu_chunk": 4, "ladder_pack": 5, "emu_onchip": 6}
 PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3, "df64": 4, "fp64emu": 5}
 METHOD = {"fp_diis": 0, "nk": 1, "pnk": 2, "ink": 3}
 

@@ -300,6 +300,12 @@ int cc_ctx_set_option(cc_ctx* ctx, int option, long long value) {
     } else if (option == CC_OPT_EMU_CHUNK) {
       CC_REQUIRE(value >= 1 && value <= 64, CC_ERR_INVALID, "CC_OPT_EMU_CHUNK: 1 to 64 k blocks");
       ctx->emu_chunk = (int)value;
+    } else if (option == CC_OPT_EMU_ONCHIP) {
+      CC_REQUIRE(value >= -1 && value <= 1, CC_ERR_INVALID, "CC_OPT_EMU_ONCHIP: -1 (by shape), 0 or 1");
+      ctx->emu_onchip = (int)value;
+    } else if (option == CC_OPT_LADDER_PACK) {
+      CC_REQUIRE(value >= -1 && value <= 1, CC_ERR_INVALID, "CC_OPT_LADDER_PACK: -1 (by shape), 0 or 1");
+      ctx->ladder_pack = (int)value;
     } else if (option == CC_OPT_GRAPHS) {
       CC_REQUIRE(value == 0 || value == 1, CC_ERR_INVALID, "CC_OPT_GRAPHS: 0 or 1");
       ctx->graphs = (int)value;

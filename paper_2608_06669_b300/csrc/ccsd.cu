@@ -65,6 +65,23 @@ size_t stage_cache_cap(int o, int v, int P) {
   return (size_t)std::min(1073741824.0, 32.0 * 4.0 * big);
 }
 
+// Whether the tensor-core ladder contracts over pairs c <= d (see Engine::ladder): per slab row,
+// the MMA time of the plain contraction (o^2 rows, padded to 128-row tiles, against v^2) against
+// that of the two pair contractions (i <= j rows against c <= d pairs, i < j against c < d)
+// plus the HBM time of the extra pass (the build's FP32 words written and read back, L+- written
+// and unpacked).
+bool ladder_pack_pays(int o, int v, cc_precision prec) {
+  const double rate = prec == CC_MIXED_BF16X3 ? 8e14 : 4e14;  // sustained MMA flop/s of one pass
+  const double passes = prec == CC_MIXED_TF32 ? 1.0 : 3.0, hbm = 6e12;
+  auto tiles = [](double rows) { return std::ceil(rows / 128.0) * 128.0; };
+  const double vv = (double)v * v, Pv = v * (v + 1) / 2.0, Qv = v * (v - 1) / 2.0;
+  const double o2 = (double)o * o, Po = o * (o + 1) / 2.0, Qo = o * (o - 1) / 2.0;
+  const double plain = 2.0 * tiles(o2) * vv * passes / rate;
+  const double packed = 2.0 * (tiles(Po) * Pv + (Qo > 0 ? tiles(Qo) * Qv : 0.0)) * passes / rate +
+                        (8.0 * vv + 16.0 * o2) / hbm;
+  return packed < plain;
+}
+
 int ladder_block_for(int v) {
   const double cap = 2.0 * 1024 * 1024 * 1024;
   const double per_a = 8.0 * (double)v * v * v;
@@ -152,30 +169,36 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
   const long long align = bf ? 64 : 32;
   const long long kpad = ((long long)v * v + align - 1) / align * align, kk = nseg * kpad;
   const int rows_pad = (ladder_block_ * v + 255) / 256 * 256;
+  // (c, d) split into the parts symmetric (+) and antisymmetric (-) under c <-> d. Since
+  // T_ij^cd = T_ji^dc, T+ is symmetric and T- antisymmetric in (i, j), so
+  // L = sum_{c<=d} W+ T+ + sum_{c<d} W- T- is contracted over pairs i <= j and c <= d only:
+  // half the flops of the (c, d) contraction. Always in FP64 and double-float (from the FP64
+  // slab); on the tensor cores when it pays (ladder_pack_pays) or is asked for, from a plain
+  // FP32 slab that one pass turns into staged W+ and W-.
+  const bool pack = tensor && (ex_.ladder_pack > 0 || (ex_.ladder_pack < 0 && ladder_pack_pays(o, v, prec)));
+  const int Po = o * (o + 1) / 2, Qo = o * (o - 1) / 2, Pv = v * (v + 1) / 2, Qv = v * (v - 1) / 2;
+  const long long kpP = ((long long)Pv + align - 1) / align * align, kpQ = ((long long)Qv + align - 1) / align * align;
+  const size_t esz = bf ? 2 : 4;
   if (tensor) {
-    const long long kmax = ((long long)v * v + 63) / 64 * 64;  // the larger of the two paddings
+    // the larger of the two paddings, and room for the two pair layouts (each padded)
+    const long long kmax = ((long long)v * v + 63) / 64 * 64 + 128;
     if (!W2_.p) W2_.alloc(ex_.pool, ((size_t)rows_pad * 3 * kmax * 4 + 7) / 8);
-    const int mode = (int)prec;
-    if (w2_mode_ != mode) {  // the k padding of this layout must read as zeros
+    const int mode = (int)prec + (pack ? 16 : 0);
+    if (w2_mode_ != mode) {  // the k padding of the plain layout must read as zeros
       CC_CUDA(cudaMemsetAsync(W2_.p, 0, W2_.n * sizeof(double), ex_.stream));
       w2_mode_ = mode;
     }
   }
   void* W2 = W2_.p;
-  // FP64 and double-float: (c, d) split into the parts symmetric (+) and antisymmetric (-)
-  // under c <-> d. Since T_ij^cd = T_ji^dc, T+ is symmetric and T- antisymmetric in (i, j), so
-  // L = sum_{c<=d} W+ T+ + sum_{c<d} W- T- is contracted over pairs i <= j and c <= d only:
-  // half the flops of the (c, d) contraction.
-  const int Po = o * (o + 1) / 2, Qo = o * (o - 1) / 2, Pv = v * (v + 1) / 2, Qv = v * (v - 1) / 2;
   double* Tp = nullptr;
   double* Tmn = nullptr;
-  if (!tensor) {
+  if (!tensor || pack) {
     const size_t nbmax = (size_t)ladder_block_ * v;
-    if (!pmW_.p) {
+    if (!pmT_.p) {
       pmT_.alloc(ex_.pool, (size_t)Po * Pv + (size_t)Qo * Qv + 1);
-      pmW_.alloc(ex_.pool, nbmax * (size_t)(Pv + Qv) + 1);
       pmL_.alloc(ex_.pool, (size_t)(Po + Qo) * nbmax + 1);
     }
+    if (!tensor && !pmW_.p) pmW_.alloc(ex_.pool, nbmax * (size_t)(Pv + Qv) + 1);
     Tp = pmT_.p;
     Tmn = Tp + (size_t)Po * Pv;
     k_ladder_pm_T(ex_, o, v, T, Tp, Tmn);
@@ -203,6 +226,32 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
                  tc);
       else if (Qo > 0)
         k_fill(ex_, (size_t)Qo * nb, 0.0, Lm);
+      k_ladder_pm_unpack(ex_, o, v, a0, al, bl, Lp, Lm, L);
+      continue;
+    }
+    if (pack) {
+      // the slab as FP32 words in W_ (row (a, b), column c v + d), split into staged W+ and W-
+      // (rows padded to rows_pad) in W2, contracted with T+ and T- over pairs, unpacked into L
+      float* Wf = reinterpret_cast<float*>(W_.p);
+      StagedOut sf{Wf, 0, 0, 0};
+      TView Wfv = view_strided(nullptr, "abcd", {al, bl, v, v}, {(long long)bl * v * v, (long long)v * v, v, 1});
+      contract(ex_, prec, 1.0, Xa, Yb, 0.0, Wfv, tb, &sf, nullptr, &stage_, fixed_xy ? 3 : 0);
+      const int nb = al * bl;
+      void* Wp2 = W2;
+      void* Wm2 = static_cast<char*>(W2) + (size_t)rows_pad * nseg * kpP * esz;
+      k_ladder_pm_stage(ex_, bf, nseg, nb, v, Wf, Wp2, kpP, Qv > 0 ? Wm2 : nullptr, kpQ);
+      double* Lp = pmL_.p;
+      double* Lm = Lp + (size_t)Po * nb;
+      StagedIn sbp{Wp2, rows_pad, (int)(nseg * kpP)};
+      contract(ex_, prec, 1.0, view(Tp, "xq", {Po, Pv}), view(W_.p, "nq", {nb, Pv}), 0.0, view(Lp, "xn", {Po, nb}), tc,
+               nullptr, &sbp);
+      if (Qo > 0 && Qv > 0) {
+        StagedIn sbm{Wm2, rows_pad, (int)(nseg * kpQ)};
+        contract(ex_, prec, 1.0, view(Tmn, "xq", {Qo, Qv}), view(W_.p, "nq", {nb, Qv}), 0.0,
+                 view(Lm, "xn", {Qo, nb}), tc, nullptr, &sbm);
+      } else if (Qo > 0) {
+        k_fill(ex_, (size_t)Qo * nb, 0.0, Lm);
+      }
       k_ladder_pm_unpack(ex_, o, v, a0, al, bl, Lp, Lm, L);
       continue;
     }

@@ -127,6 +127,8 @@ struct Exec {
   long long stage_cap = -1;                    // bytes of kept staged operands (-1: the default)
   int graphs = 1;                              // replay the JVPs of a solve from CUDA graphs
   int emu_chunk = 64;                          // k blocks of 64 per exact chunk of the FP64 emulation
+  int ladder_pack = -1;                        // (c, d) split of the tensor-core ladder: -1 by shape, 0, 1
+  int emu_onchip = -1;                         // FP64 emulation summed on chip: -1 by shape, 0, 1
   void count(uint64_t k = 1) const {
     if (launches) *launches += k;
     if (calls) *calls += 1;
@@ -136,6 +138,20 @@ struct Exec {
   void mark_begin(cudaEvent_t* a) const;
   void mark_end(const char* tag, cudaEvent_t a, double flops) const;
 };
+
+// Digit slices per operand of the FP64 emulation (CC_FP64_EMU): 9 slices of 6 bits keep 54
+// significant bits below each row's largest element, one more than FP64's significand; the
+// S (S + 1) / 2 slice products of levels 2..S + 1 run on the tensor cores.
+constexpr int kOzSlices = 9;
+constexpr int kOzProducts = kOzSlices * (kOzSlices + 1) / 2;
+
+// Pair indices, row-major over the upper triangle: c <= d (with the diagonal) and c < d.
+__host__ __device__ __forceinline__ size_t pair_le(int c, int d, int n) {
+  return (size_t)c * (2 * n - c + 1) / 2 + (d - c);
+}
+__host__ __device__ __forceinline__ size_t pair_lt(int c, int d, int n) {
+  return (size_t)c * (2 * n - c - 1) / 2 + (d - c - 1);
+}
 
 // ---------------------------------------------------------------------------
 // GEMM with compound indices of up to three strided modes:
@@ -189,7 +205,8 @@ struct CWalk {
 struct StagedOut {  // C written in that layout (C's strides count elements), beta must be 0
   void* base;
   long long kpad;
-  int nseg, seg_lo;  // seg_lo: bit mask of the segments that hold the low part
+  int nseg, seg_lo;  // seg_lo: bit mask of the segments that hold the low part; nseg = 0: C as
+                     // plain FP32 words
 };
 struct StagedIn {  // the B operand already staged (rows padded to the tile, zero k padding)
   const void* base;
@@ -310,6 +327,9 @@ void k_ladder_mirror_add(const Exec& ex, int o, int v, int blk, const double* L,
 // The ladder's symmetric/antisymmetric split over (c, d): pair-packed T+, T- (rows i <= j and
 // i < j), W+, W- (per slab row), and the block of L rebuilt from L+ and L-
 void k_ladder_pm_T(const Exec& ex, int o, int v, const double* T, double* Tp, double* Tm);
+// the tensor-core ladder's (c, d) split: W+ and W- of FP32 slab rows, written staged
+void k_ladder_pm_stage(const Exec& ex, bool bf, int nseg, long long rows, int v, const float* W, void* Wp,
+                       long long kpP, void* Wm, long long kpQ);
 void k_ladder_pm_W(const Exec& ex, size_t rows, int v, const double* W, double* Wp, double* Wm);
 void k_ladder_pm_unpack(const Exec& ex, int o, int v, int a0, int al, int bl, const double* Lp, const double* Lm,
                         double* L);

@@ -419,11 +419,12 @@ bool tc_faster(const Exec& ex, cc_precision prec, const GemmArgs& g) {
                         ((g.K + tk - 1) / tk * (double)tk) * nseg * g.batch;
   double t_tc = 12e-6 + padded / 4.5e14 + 8.0 * g.M * (double)g.N * g.batch / 1e12;
   if (prec == CC_FP64_EMU) {
-    // 36 slice products on kind::f16, the exact partial sums (one per chunk of up to 1024 k,
-    // written and read once in FP32), the digit staging of both operands
-    const double kp = (g.K + 63) / 64 * 64.0, chunks = 36.0 * kp / 1024.0 + 8.0;
-    t_tc = 20e-6 + 36.0 * padded / 1.2e15 + chunks * 8.0 * g.M * (double)g.N * g.batch / 5e12 +
-           ((double)g.M + g.N) * kp * g.batch * 24.0 / 5e12;
+    // the slice products on kind::f16, the exact partial sums (one per chunk of up to 4096 k,
+    // written and read once in FP32; none when they are summed on chip, so this is an upper
+    // bound), the digit staging of both operands
+    const double kp = (g.K + 63) / 64 * 64.0, chunks = kOzProducts * kp / 4096.0 + kOzSlices;
+    t_tc = 20e-6 + kOzProducts * padded / 1.2e15 + chunks * 8.0 * g.M * (double)g.N * g.batch / 5e12 +
+           ((double)g.M + g.N) * kp * g.batch * (8.0 + 2.0 * kOzSlices) / 5e12;
   }
   // the FP64 kernel's parallelism: 16 x 16 tiles, k split at most 64 ways
   const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch * std::min(64, std::max(1, g.K / 32));

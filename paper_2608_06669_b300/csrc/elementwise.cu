@@ -74,10 +74,6 @@ __global__ void ladder_mirror_add_kernel(int o, int v, int blk, const double* __
   }
 }
 
-// Pair indices, row-major over the upper triangle: c <= d (with the diagonal) and c < d.
-__device__ __forceinline__ size_t pair_le(int c, int d, int n) { return (size_t)c * (2 * n - c + 1) / 2 + (d - c); }
-__device__ __forceinline__ size_t pair_lt(int c, int d, int n) { return (size_t)c * (2 * n - c - 1) / 2 + (d - c - 1); }
-
 // T+[(i<=j)][(c<=d)] = (T_ij^cd + T_ij^dc) / 2 (T_ij^cc on the diagonal), T-[(i<j)][(c<d)] =
 // (T_ij^cd - T_ij^dc) / 2, for T with T_ij^cd = T_ji^dc
 __global__ void ladder_pm_T_kernel(int o, int v, const double* __restrict__ T, double* __restrict__ Tp,

@@ -162,13 +162,70 @@ __global__ void tc_splitk_reduce_kernel(GemmArgs g, const float* __restrict__ pa
 #pragma unroll 8
       for (int p = 0; p < splits; ++p) s += (double)pr[(size_t)p * tot + n];
       const long long off = rowoff + cw.off;
-      if (Cs) {
+      if (Cs && nseg == 0) {  // plain FP32 words
+        reinterpret_cast<float*>(Cs)[off] = (float)(g.alpha * s);
+      } else if (Cs) {
         store_staged(Cs + off, kpad, nseg, seglo, (float)(g.alpha * s));
       } else {
         double* c = g.C + off;
         *c = g.beta == 0.0 ? g.alpha * s : fma(g.beta, *c, g.alpha * s);
       }
       cw.step(g.cn, 32);
+    }
+  }
+}
+
+// The (c, d) split of the tensor-core ladder's slab. W holds rows r of v x v FP32 values
+// (column c v + d) as the build GEMM wrote them; W+[r][pair_le(c, d)] = W_r^cd + W_r^dc (W_r^cc
+// on the diagonal) and W-[r][pair_lt(c, d)] = W_r^cd - W_r^dc are written in staging layout:
+// nseg segments of kpP (kpQ) elements per row ([hi|lo|hi] for three), zero past the last pair.
+// One 256-thread block per (row, 32 x 32 block pair with c-block <= d-block) at a time: the
+// blocks W^(c0.., d0..) and W^(d0.., c0..) are both read along rows into shared memory, so the
+// loads and the stores (consecutive d for one c) are coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) ladder_pm_stage_kernel(long long rows, int v, const float* __restrict__ W,
+                                                              T* __restrict__ Wp, long long kpP, T* __restrict__ Wm,
+                                                              long long kpQ, int nseg) {
+  __shared__ float xs[32][33], ys[32][33];
+  const int nt = (v + 31) / 32, npairs = nt * (nt + 1) / 2;
+  const long long Pv = (long long)v * (v + 1) / 2, Qv = (long long)v * (v - 1) / 2;
+  const int seglo = nseg == 3 ? 0b010 : 0;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long vv = (long long)v * v, items = rows * npairs;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const long long r = it / npairs;
+    const int q0 = (int)(it - r * npairs);
+    int q = q0, cb = 0;
+    while (q >= nt - cb) {  // q -> (cb <= db), row-major over the block pairs
+      q -= nt - cb;
+      ++cb;
+    }
+    const int c0 = cb * 32, d0 = (cb + q) * 32;
+    const float* Wr = W + r * vv;
+    __syncthreads();  // the previous item's reads of xs and ys are done
+    for (int i = ty; i < 32; i += 8) {
+      const int c = c0 + i, d = d0 + tx;
+      xs[i][tx] = (c < v && d < v) ? Wr[(long long)c * v + d] : 0.f;  // W^(c0 + i, d0 + tx)
+      const int d1 = d0 + i, c1 = c0 + tx;
+      ys[i][tx] = (d1 < v && c1 < v) ? Wr[(long long)d1 * v + c1] : 0.f;  // W^(d0 + i, c0 + tx)
+    }
+    __syncthreads();
+    T* wp = Wp + r * nseg * kpP;
+    T* wm = Wm ? Wm + r * nseg * kpQ : nullptr;
+    for (int i = ty; i < 32; i += 8) {
+      const int c = c0 + i, d = d0 + tx;
+      if (c >= v || d >= v || d < c) continue;
+      const float x = xs[i][tx], y = ys[tx][i];  // W^cd and W^dc
+      store_staged(wp + pair_le(c, d, v), kpP, nseg, seglo, c < d ? __fadd_rn(x, y) : x);
+      if (wm && c < d) store_staged(wm + pair_lt(c, d, v), kpQ, nseg, seglo, __fsub_rn(x, y));
+    }
+    if (q0 == 0) {  // the row's k padding (fewer than 64 elements per segment)
+      T zero, zlo;
+      split(0.f, zero, zlo);
+      const int padP = (int)(kpP - Pv), padQ = (int)(kpQ - Qv);
+      for (int e = threadIdx.x; e < nseg * padP; e += blockDim.x) wp[(e / padP) * kpP + Pv + e % padP] = zero;
+      if (wm)
+        for (int e = threadIdx.x; e < nseg * padQ; e += blockDim.x) wm[(e / padQ) * kpQ + Qv + e % padQ] = zero;
     }
   }
 }
@@ -189,19 +246,41 @@ __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
 // FP64-accurate products on the tensor cores: Ozaki's error-free splitting (Ozaki, Ogita,
 // Oishi and Rump, Numer. Algorithms 59 (2012) 95; on tensor cores: Mukunoki, Ozaki, Ogita and
 // Imamura, ICCS 2020). Every row x of an operand (a row of A, a column of B) is written as
-//   x_k = sign(x_k) sum_{s=1..S} d_s(x_k) 2^(sigma - OZ_BETA s) + (error < 2^(sigma - OZ_BETA S)),
-// with sigma the row's exponent (|x_k| < 2^sigma) and integer digits 0 <= d_s < 2^OZ_BETA, which
-// BF16 holds exactly. A product of two digit slices is then a sum of integers: each MMA chunk of
-// at most nk k blocks sums at most nk * 64 products below 2^(2 OZ_BETA), an integer below 2^22
-// for the default nk = 16 (below 2^24 up to nk = 64), which the FP32 accumulator represents
-// exactly. The slice products of one level L = s + t share the
+//   x_k = sign(x_k) sum_{s=1..S} d_s(x_k) 2^(sigma - OZ_BETA s) + (error <= 2^(sigma - OZ_BETA S - 1)),
+// with sigma the row's exponent (|x_k| < 2^sigma): |x_k| is rounded to the nearest multiple of
+// 2^(sigma - OZ_BETA S), so the representation error has no sign bias and sums of many products
+// grow like their square root, not like their count. The digits are integers 0 <= d_s < 2^OZ_BETA
+// (d_1 <= 2^OZ_BETA when the rounding carries into it), which BF16 holds exactly. A product of
+// two digit slices is then a sum of integers: each MMA chunk of at most nk k blocks sums at most
+// nk * 64 products of at most 2^(2 OZ_BETA), an integer of at most 2^24 up to nk = 64, which the
+// FP32 accumulator represents exactly. The slice products of one level L = s + t share the
 // scale 2^(sigma_i + tau_j - OZ_BETA L); levels up to S + 1 are kept (the first term dropped is
-// below 2^(-OZ_BETA S) of the leading one) and added in 64-bit integer fixed point, so the only
-// rounding is the final conversion to FP64.
+// below 2^(-OZ_BETA S) of the leading one) and added exactly in two 64-bit integer fixed-point
+// sums (oz_fixed_value), so the only rounding is the final conversion to FP64.
 // ---------------------------------------------------------------------------
-constexpr int OZ_S = 8;      // slices per operand: 48 significant bits
+constexpr int OZ_S = kOzSlices;  // slices per operand: 54 significant bits
 constexpr int OZ_BETA = 6;   // bits per slice digit
-constexpr int OZ_NK = 64;    // default k blocks (of 64) per exact FP32 chunk: 64 * 64 * 63^2 < 2^24
+constexpr int OZ_NK = 64;    // default k blocks (of 64) per exact FP32 chunk: 64 * 64 * 64^2 = 2^24
+
+// |x| of an FP64 bit pattern in units of 2^(sigma - OZ_BETA S), rounded to nearest (ties away
+// from zero), for a row whose largest biased exponent is em (sigma = em - 1022): the digits of
+// the result are the slices. Integer shifts only; at most 2^(OZ_BETA S).
+__device__ __forceinline__ unsigned long long oz_quantize(unsigned long long bits, unsigned em) {
+  unsigned e = (unsigned)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  if (e) m |= 1ull << 52;
+  else e = 1;
+  // |x| = m 2^(e - 1075) = m 2^-sh units, sh = em - e + 53 - beta S (at least 53 - beta S = -1:
+  // then the shift is exact)
+  const int sh = (int)em - (int)e + 53 - OZ_BETA * OZ_S;
+  if (sh <= 0) return m << (-sh);
+  return sh >= 64 ? 0ull : ((m + (1ull << (sh - 1))) >> sh);
+}
+// slice sl (1 = leading) of a quantised magnitude; the leading digit keeps a rounding carry
+__device__ __forceinline__ int oz_digit(unsigned long long qv, int sl) {
+  const unsigned long long d = qv >> (OZ_BETA * (OZ_S - sl));
+  return sl == 1 ? (int)d : (int)(d & ((1u << OZ_BETA) - 1));
+}
 
 // Pass 1 of the digit staging: the largest biased exponent of every staged row (a row of A or
 // a column of B), one warp per piece of ROW_PIECE elements of a row, combined by an integer
@@ -265,18 +344,12 @@ __global__ void oz_digits_kernel(const double* __restrict__ src, CIdx rix, CIdx 
       unsigned long long qv = 0, neg = 0;
       if (k < K) {
         const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
-        unsigned e = (unsigned)((bits >> 52) & 0x7FF);
-        unsigned long long m = bits & ((1ull << 52) - 1);
-        if (e) m |= 1ull << 52;
-        else e = 1;
         neg = bits >> 63;
-        // |x| = m 2^(e - 1075); in units of 2^(sigma - beta S): m >> (em - e + 53 - beta S)
-        const unsigned sh = em - e + 53 - OZ_BETA * OZ_S;
-        qv = sh >= 64 ? 0ull : (m >> sh);
+        qv = oz_quantize(bits, em);
       }
 #pragma unroll
       for (int sl = 1; sl <= OZ_S; ++sl) {
-        const int d = (int)((qv >> (OZ_BETA * (OZ_S - sl))) & ((1u << OZ_BETA) - 1));
+        const int d = oz_digit(qv, sl);
         const float f = neg ? -(float)d : (float)d;
         const int seg = rev ? OZ_S - sl : sl - 1;
         row[(size_t)seg * k_pad + k] = __float2bfloat16_rn(f);
@@ -323,17 +396,12 @@ __global__ void oz_stage_rows_kernel(const double* __restrict__ src, CIdx rix, C
       unsigned long long qv = 0, neg = 0;
       if (k < K) {
         const unsigned long long bits = (unsigned long long)__double_as_longlong(srow[kw.off]);
-        unsigned ex = (unsigned)((bits >> 52) & 0x7FF);
-        unsigned long long m = bits & ((1ull << 52) - 1);
-        if (ex) m |= 1ull << 52;
-        else ex = 1;
         neg = bits >> 63;
-        const unsigned sh = em - ex + 53 - OZ_BETA * OZ_S;
-        qv = sh >= 64 ? 0ull : (m >> sh);
+        qv = oz_quantize(bits, em);
       }
 #pragma unroll
       for (int sl = 1; sl <= OZ_S; ++sl) {
-        const int d = (int)((qv >> (OZ_BETA * (OZ_S - sl))) & ((1u << OZ_BETA) - 1));
+        const int d = oz_digit(qv, sl);
         const float f = neg ? -(float)d : (float)d;
         const int seg = rev ? OZ_S - sl : sl - 1;
         row[(size_t)seg * k_pad + k] = __float2bfloat16_rn(f);
@@ -349,11 +417,28 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// The levels' exact sums in fixed point without any rounding: levels 2..OZ_LH go into acc_h in
+// units of level OZ_LH, the rest into acc_l in units of level S + 1, each level's sum shifted by
+// OZ_BETA bits per level below its group's unit. With products of at most 2^12 and level L
+// holding (L - 1) k_pad of them, |acc_h| <= k_pad 2^30.1 and |acc_l| <= k_pad 2^38.3, inside
+// int64 for k_pad < 2^24. The value in units of level S + 1 is acc_h 2^OZ_HSH + acc_l.
+constexpr int OZ_LH = 5;
+constexpr int OZ_HSH = OZ_BETA * (OZ_S + 1 - OZ_LH);
+__device__ __forceinline__ int oz_level_shift(int L) {
+  return L <= OZ_LH ? OZ_BETA * (OZ_LH - L) : OZ_BETA * (OZ_S + 1 - L);
+}
+// acc_h 2^OZ_HSH + acc_l as a double: the exact sum is hi 2^OZ_HSH + lo with 0 <= lo < 2^OZ_HSH;
+// hi is exact in FP64 (|hi| < 2^53 for k_pad < 2^22), so the one rounding is the fma's.
+__device__ __forceinline__ double oz_fixed_value(long long acc_h, long long acc_l) {
+  const long long hi = acc_h + (acc_l >> OZ_HSH);
+  const long long lo = acc_l & ((1ll << OZ_HSH) - 1);
+  return fma((double)hi, (double)(1ll << OZ_HSH), (double)lo);
+}
+
 // C = alpha * sum over levels of the exact chunk sums (scaled per level) + beta * C. One warp
-// per piece of an output row; the chunk sums are integers below 2^22, added per level in int64
-// and combined in 64-bit fixed point with the levels' scales 2^(OZ_BETA (S + 1 - L) - gsh)
-// (gsh > 0 drops low bits of the smallest levels so that the sum stays below 2^62).
-__global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, int kseg, int nk, int gsh,
+// per piece of an output row; the chunk sums are integers of at most 2^24, added per level and
+// into the two fixed-point accumulators above, converted once to FP64.
+__global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, int kseg, int nk,
                                   const unsigned* __restrict__ expA, int rowsA_pad, const unsigned* __restrict__ expB,
                                   int rowsB_pad, int piece) {
   const int lane = threadIdx.x & 31;
@@ -369,26 +454,27 @@ __global__ void oz_combine_kernel(GemmArgs g, const float* __restrict__ part, in
     const long long rowoff = cidx(g.cb, b) + cidx(g.cm, m);
     const float* pr = part + (size_t)qrow * g.N;
     const int ea = (int)max(expA[(size_t)b * rowsA_pad + m], 1u) - 1022;  // sigma of row m
-    // alpha 2^(sigma_m - beta (S + 1) + gsh) for the row, 2^tau_n per column: the scaling is two
+    // alpha 2^(sigma_m - beta (S + 1)) for the row, 2^tau_n per column: the scaling is two
     // multiplications by exact powers of two while their exponents are inside the normal range
-    const int er = ea - OZ_BETA * (OZ_S + 1) + gsh;
+    const int er = ea - OZ_BETA * (OZ_S + 1);
     const double row_scale = g.alpha * pow2(er);
     CWalk cw;
     cw.init(g.cn, n0 + lane);
     for (int n = n0 + lane; n < n1; n += 32) {
-      long long acc = 0;
+      long long acc_h = 0, acc_l = 0;
       int v = 0;
       for (int L = 2; L <= OZ_S + 1; ++L) {
         const int nch = ((L - 1) * kseg + nk - 1) / nk;
         long long lv = 0;
         for (int c = 0; c < nch; ++c, ++v) lv += (long long)__float2int_rn(pr[(size_t)v * tot + n]);
-        const int sh = OZ_BETA * (OZ_S + 1 - L) - gsh;
-        acc += sh >= 0 ? (lv << sh) : ((lv + (1ll << (-sh - 1))) >> (-sh));
+        if (L <= OZ_LH) acc_h += lv << oz_level_shift(L);
+        else acc_l += lv << oz_level_shift(L);
       }
+      const double x = oz_fixed_value(acc_h, acc_l);
       const int eb = (int)max(expB[(size_t)b * rowsB_pad + n], 1u) - 1022;
       const double val = (er > -960 && er < 960 && eb > -960 && eb < 960 && er + eb > -960 && er + eb < 960)
-                             ? (double)acc * row_scale * pow2(eb)
-                             : g.alpha * ldexp((double)acc, er + eb);
+                             ? x * row_scale * pow2(eb)
+                             : g.alpha * ldexp(x, er + eb);
       double* c = g.C + rowoff + cw.off;
       *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
       cw.step(g.cn, 32);
@@ -554,9 +640,10 @@ constexpr size_t SMEM_USED =
     (size_t)STAGES * (A_BYTES + B_BYTES) + EPI_WARPS * EP_FLOATS * 4 + (2 * STAGES + 4) * 8 + 16;
 static_assert(1024 + SMEM_USED <= 232448, "shared memory beyond 227 KB");
 
-// What the epilogue writes: C in FP64 (alpha acc + beta C), split-k FP32 partial sums, or the
-// staging layout of a later contraction with one segment or three ([hi|lo|hi]).
-enum { EPI_F64 = 0, EPI_PART = 1, EPI_STAGED1 = 2, EPI_STAGED3 = 3 };
+// What the epilogue writes: C in FP64 (alpha acc + beta C), split-k FP32 partial sums, the
+// staging layout of a later contraction with one segment or three ([hi|lo|hi]), or C as plain
+// FP32 words (alpha acc) at the compound offsets of C.
+enum { EPI_F64 = 0, EPI_PART = 1, EPI_STAGED1 = 2, EPI_STAGED3 = 3, EPI_F32 = 4, EPI_COUNT = 5 };
 constexpr size_t SMEM_BYTES = 1024 + SMEM_USED;
 
 // Persistent, warp-specialised GEMM: each CTA walks tiles blockIdx.x, +gridDim.x, ...
@@ -725,6 +812,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
             if (ro >= 0 && n_ok) g.part[ro + n] = tile[rr * 33 + lane];
           }
+        } else if constexpr (EPI == EPI_F32) {
+          float* cs = static_cast<float*>(g.Cs) + (n_ok ? cidx(g.cn, n) : 0);
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) {
+            const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
+            if (ro >= 0 && n_ok) cs[ro] = alpha_f * tile[rr * 33 + lane];
+          }
         } else if constexpr (EPI == EPI_STAGED1 || EPI == EPI_STAGED3) {
           T* cs = static_cast<T*>(g.Cs) + (n_ok ? cidx(g.cn, n) : 0);
           const long long kpad = g.cs_kpad;
@@ -763,6 +857,297 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// On-chip recombination of the FP64 emulation: one persistent launch whose tile is a 128 x 128
+// block of C and whose work per tile is every (level, chunk) slice product in turn, level by
+// level. The MMA thread alternates two FP32 accumulators over a tile's slice products; the
+// epilogue warps read each exact chunk sum once and add it, shifted for its level, into a 64-bit
+// fixed-point sum in registers (64 columns of one row per thread), so no partial sum leaves the
+// SM. After the last level of the first group (oz_fixed_value) the register sums go to TMEM and
+// the second group starts from zero; the two are joined at the end. Same integers, same single
+// rounding as oz_combine_kernel: the result is the same bits.
+// ---------------------------------------------------------------------------
+constexpr int OZ_TN = 128;
+constexpr int OZ_STAGES = 5;
+constexpr uint32_t OZ_B_BYTES = OZ_TN * 128;
+constexpr uint32_t OZ_EP_DOUBLES = 32 * 17;  // per epilogue warp: 32 rows x 16 columns (+1 pad)
+constexpr size_t OZ_SMEM_BYTES = 1024 + (size_t)OZ_STAGES * (A_BYTES + OZ_B_BYTES) +
+                                 EPI_WARPS * OZ_EP_DOUBLES * 8 + (2 * OZ_STAGES + 4) * 8 + 16;
+static_assert(OZ_SMEM_BYTES <= 232448, "shared memory beyond 227 KB");
+constexpr uint32_t OZ_TMEM_COLS = 512;  // two accumulators of 128 columns; the first group's int64 sums
+
+struct OzArgs {
+  int M, N, num_m, num_n, tiles, batch, m_fast;
+  int kseg, nk, nsplit;
+  CIdx cm, cn, cb;
+  double alpha, beta;
+  double* C;
+  const unsigned* expA;  // biased exponent maxima of A's rows and B's columns
+  const unsigned* expB;
+  int rowsA_pad, rowsB_pad;
+  int* err;
+  unsigned long long wait_ns;
+};
+
+// instruction descriptor: D = F32, A = B = BF16, both K-major, N = OZ_TN, M = TM
+constexpr uint32_t oz_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void oz_tile(const OzArgs& a, int t, int& bz, int& m0, int& n0) {
+  const int per = a.num_m * a.num_n;
+  bz = t / per;
+  const int r = t - bz * per;
+  if (a.m_fast) {
+    m0 = (r % a.num_m) * TM;
+    n0 = (r / a.num_m) * OZ_TN;
+  } else {
+    m0 = (r / a.num_n) * TM;
+    n0 = (r % a.num_n) * OZ_TN;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+// waits for this thread's TMEM loads; the registers are operands, so no use of them moves above
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16], uint32_t (&s)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4]), "+r"(s[5]), "+r"(s[6]), "+r"(s[7]), "+r"(s[8]), "+r"(s[9]), "+r"(s[10]), "+r"(s[11]), "+r"(s[12]), "+r"(s[13]), "+r"(s[14]), "+r"(s[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ OzArgs a) {
+  constexpr int TK = Elt<true>::TK, UK = Elt<true>::UK;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + OZ_STAGES * A_BYTES;
+  double* ep = reinterpret_cast<double*>(sB + OZ_STAGES * OZ_B_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ep + EPI_WARPS * OZ_EP_DOUBLES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + OZ_STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * OZ_STAGES), tempty0 = smem_u32(bars + 2 * OZ_STAGES + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, EPI_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  const unsigned long long wait_ns = a.wait_ns;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t q = 0;
+      for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
+        int bz, m0, n0;
+        oz_tile(a, t, bz, m0, n0);
+        for (int sp = 0; sp < a.nsplit && ok; ++sp) {
+          int kA0, kB0, nkb;
+          oz_split_range(OZ_S, a.kseg, a.nk, sp, kA0, kB0, nkb);
+          for (int kb = 0; kb < nkb; ++kb, ++q) {
+            const int s = q % OZ_STAGES;
+            const uint32_t ph = (q / OZ_STAGES) & 1;
+            if (!mbar_wait(empty0 + 8 * s, ph ^ 1, wait_ns)) { ok = false; break; }
+            mbar_expect_tx(full0 + 8 * s, A_BYTES + OZ_B_BYTES);
+            tma_load_3d(smem_u32(sA + s * A_BYTES), &tmA, full0 + 8 * s, (kA0 + kb) * TK, m0, bz);
+            tma_load_3d(smem_u32(sB + s * OZ_B_BYTES), &tmB, full0 + 8 * s, (kB0 + kb) * TK, n0, bz);
+          }
+        }
+      }
+      for (uint32_t r = q > (uint32_t)OZ_STAGES ? q - OZ_STAGES : 0; r < q; ++r)
+        if (!mbar_wait(full0 + 8 * (r % OZ_STAGES), (r / OZ_STAGES) & 1, wait_ns)) ok = false;
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t q = 0, u = 0;  // pipeline slots; slice products (accumulator uses)
+      for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
+        for (int sp = 0; sp < a.nsplit; ++sp, ++u) {
+          const int acc = u & 1;
+          if (!mbar_wait(tempty0 + 8 * acc, ((u >> 1) & 1) ^ 1, wait_ns)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(acc * OZ_TN);
+          int kA0, kB0, nkb;
+          oz_split_range(OZ_S, a.kseg, a.nk, sp, kA0, kB0, nkb);
+          for (int kb = 0; kb < nkb; ++kb, ++q) {
+            const int s = q % OZ_STAGES;
+            if (!mbar_wait(full0 + 8 * s, (q / OZ_STAGES) & 1, wait_ns)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * OZ_B_BYTES);
+#pragma unroll
+            for (int j = 0; j < TK / UK; ++j) {
+              const uint64_t da = sdesc(a0 + j * 32), db = sdesc(b0 + j * 32);
+              const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "l"(da), "l"(db), "r"(oz_idesc()), "r"(accum)
+                  : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                         : "memory");
+          }
+          if (!ok) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tfull0 + 8 * acc)
+                       : "memory");
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    const int quad = warp & 3;         // TMEM lanes = tile rows quad * 32 .. + 31
+    const int half = (warp - 2) >> 2;  // columns half * 64 .. + 63 of the tile
+    double* tile = ep + (warp - 2) * OZ_EP_DOUBLES;
+    const uint32_t lanes = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint32_t thigh = lanes + 2 * OZ_TN + half * 128;  // the first group's sums: 64 int64
+    uint32_t u = 0;
+    for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
+      int bz, m0, n0;
+      oz_tile(a, t, bz, m0, n0);
+      long long acc[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) acc[j] = 0;
+      bool high = true;  // summing the first group of levels
+      for (int sp = 0; sp < a.nsplit; ++sp, ++u) {
+        int kA0, kB0, nkb;
+        const int L = oz_split_range(OZ_S, a.kseg, a.nk, sp, kA0, kB0, nkb);
+        if (high && L > OZ_LH) {  // first group done: park its sums in TMEM, start the second
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            uint32_t w[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              w[2 * j] = (uint32_t)(unsigned long long)acc[p * 8 + j];
+              w[2 * j + 1] = (uint32_t)((unsigned long long)acc[p * 8 + j] >> 32);
+            }
+            tmem_st16(thigh + p * 16, w);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 64; ++j) acc[j] = 0;
+          high = false;
+        }
+        const int sh = oz_level_shift(L);
+        const int buf = u & 1;
+        bool got = mbar_wait(tfull0 + 8 * buf, (u >> 1) & 1, wait_ns);
+        got = __all_sync(0xffffffffu, got);
+        if (!got) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tacc = lanes + buf * OZ_TN + half * 64;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          uint32_t r[16];
+          tmem_ld16(tacc + p * 16, r);
+          tmem_wait_ld(r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[p * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+        }
+        // the accumulator goes back to the MMA thread
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+      }
+      if (!ok) break;
+      // C = alpha 2^(sigma_m + tau_n - beta (S + 1)) (acc_h 2^OZ_HSH + acc_l) + beta C, as in
+      // oz_combine_kernel. A thread holds one row: 16 columns at a time go through shared memory
+      // so that a warp's stores run along rows of C (two rows of 16 columns per store).
+      const int my_row = m0 + quad * 32 + lane;
+      long long my_off = -1;
+      int my_er = 0;
+      if (my_row < a.M) {
+        my_off = cidx(a.cb, bz) + cidx(a.cm, my_row);
+        my_er = (int)max(a.expA[(size_t)bz * a.rowsA_pad + my_row], 1u) - 1022 - OZ_BETA * (OZ_S + 1);
+      }
+      const bool rows_left = m0 + quad * 32 < a.M;  // warp-uniform
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int c0 = n0 + half * 64 + p * 16;
+        if (!rows_left || c0 >= a.N) break;  // warp-uniform
+        uint32_t w0[16], w1[16];
+        tmem_ld16(thigh + p * 32, w0);
+        tmem_ld16(thigh + p * 32 + 16, w1);
+        tmem_wait_ld(w0, w1);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t lo32 = j < 8 ? w0[2 * j] : w1[2 * (j - 8)];
+          const uint32_t hi32 = j < 8 ? w0[2 * j + 1] : w1[2 * (j - 8) + 1];
+          const long long acc_h = (long long)(((unsigned long long)hi32 << 32) | lo32);
+          tile[lane * 17 + j] = oz_fixed_value(acc_h, acc[p * 16 + j]);
+        }
+        __syncwarp();
+        const int col = c0 + (lane & 15);
+        const bool n_ok = col < a.N;
+        int eb = 0;
+        long long coff = 0;
+        if (n_ok) {
+          eb = (int)max(a.expB[(size_t)bz * a.rowsB_pad + col], 1u) - 1022;
+          coff = cidx(a.cn, col);
+        }
+#pragma unroll 4
+        for (int r0 = 0; r0 < 32; r0 += 2) {
+          const int row = r0 + (lane >> 4);
+          const long long ro = __shfl_sync(0xffffffffu, my_off, row);
+          const int er = __shfl_sync(0xffffffffu, my_er, row);
+          if (ro >= 0 && n_ok) {
+            const double x = tile[row * 17 + (lane & 15)];
+            const double row_scale = a.alpha * pow2(er);
+            const double val = (er > -960 && er < 960 && eb > -960 && eb < 960 && er + eb > -960 && er + eb < 960)
+                                   ? x * row_scale * pow2(eb)
+                                   : a.alpha * ldexp(x, er + eb);
+            double* c = a.C + ro + coff;
+            *c = a.beta == 0.0 ? val : fma(a.beta, *c, val);
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (!ok) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
 }
 
 // Self-test of the bounded waits: one thread waits on an mbarrier that expects one arrival
@@ -812,12 +1197,12 @@ namespace {
 // The dynamic shared-memory opt-in is per device and per kernel instance; server threads may
 // race here, so the per-device bits are atomic.
 template <typename K>
-void ensure_smem_attr(K kern, std::atomic<uint64_t>& done) {
+void ensure_smem_attr(K kern, std::atomic<uint64_t>& done, size_t bytes = SMEM_BYTES) {
   int dev = 0;
   CC_CUDA(cudaGetDevice(&dev));
   const uint64_t bit = 1ull << (dev & 63);
   if (!(done.load() & bit)) {
-    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     done.fetch_or(bit);
   }
 }
@@ -968,9 +1353,9 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
   if (splits > 1) {
     job.epi = EPI_PART;
   } else if (g.so) {
-    CC_REQUIRE((g.so->nseg == 1 && g.so->seg_lo == 0) || (g.so->nseg == 3 && g.so->seg_lo == 0b010), CC_ERR_INVALID,
-               "staged output layout not supported by the tensor-core epilogue");
-    job.epi = g.so->nseg == 3 ? EPI_STAGED3 : EPI_STAGED1;
+    CC_REQUIRE(g.so->nseg == 0 || (g.so->nseg == 1 && g.so->seg_lo == 0) || (g.so->nseg == 3 && g.so->seg_lo == 0b010),
+               CC_ERR_INVALID, "staged output layout not supported by the tensor-core epilogue");
+    job.epi = g.so->nseg == 0 ? EPI_F32 : g.so->nseg == 3 ? EPI_STAGED3 : EPI_STAGED1;
   }
 }
 
@@ -1005,6 +1390,7 @@ void tc_launch(const Exec& ex, int epi, TcJob<BF>* const* jobs, int n) {
     case EPI_PART: tc_launch_group<BF, EPI_PART, MAXP>(ex, jobs, n); break;
     case EPI_STAGED1: tc_launch_group<BF, EPI_STAGED1, MAXP>(ex, jobs, n); break;
     case EPI_STAGED3: tc_launch_group<BF, EPI_STAGED3, MAXP>(ex, jobs, n); break;
+    case EPI_F32: tc_launch_group<BF, EPI_F32, MAXP>(ex, jobs, n); break;
     default: tc_launch_group<BF, EPI_F64, MAXP>(ex, jobs, n); break;
   }
 }
@@ -1048,7 +1434,7 @@ void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>
     jobs.emplace_back(new TcJob<BF>());
     tc_prepare<BF>(ex, prec, g, *jobs.back());
   }
-  for (int epi = 0; epi < 4; ++epi) {
+  for (int epi = 0; epi < EPI_COUNT; ++epi) {
     std::vector<TcJob<BF>*> sel;
     for (auto& j : jobs)
       if (j->epi == epi) sel.push_back(j.get());
@@ -1071,13 +1457,34 @@ int oz_splits(int kseg, int nk) {
   return n;
 }
 
+// Which form of the emulated product runs: on chip (oz_gemm_kernel: 128 x 128 tiles, every slice
+// product of a tile on one SM, no partial sums) or through FP32 partial sums (every (level, chunk)
+// slice product of a 128 x 256 tile a split of its own, then oz_combine_kernel). The first moves
+// 8 bytes less per output and slice product but spreads only the output tiles over the SMs;
+// a time model of both decides.
+bool oz_onchip(const Exec& ex, const GemmArgs& g, int kseg, int nsplit) {
+  if (ex.emu_onchip >= 0) return ex.emu_onchip == 1;
+  const double sms = ex.sm_count, rate = 1.6e13, hbm = 6e12;  // BF16 MMA flop/s of one SM; HBM B/s
+  const double kblocks = (double)kOzProducts * kseg;             // k blocks of a tile's slice products
+  const double t128 = 2.0 * TM * OZ_TN * 64.0 * kblocks / rate + 2e-6;
+  const double tiles128 = (double)g.batch * std::ceil(g.M / (double)TM) * std::ceil(g.N / (double)OZ_TN);
+  const double onchip = std::ceil(tiles128 / sms) * t128;
+  const double tiles256 = (double)g.batch * std::ceil(g.M / (double)TM) * std::ceil(g.N / (double)TN);
+  const double tsplit = 2.0 * TM * TN * 64.0 * kblocks / nsplit / rate + 1e-6;
+  const double parts = std::ceil(tiles256 * nsplit / sms) * tsplit + 8.0 * nsplit * g.batch * g.M * (double)g.N / hbm + 5e-6;
+  return onchip < parts;
+}
+
 void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   constexpr int TK = Elt<true>::TK;
-  const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
   const int k_pad = (g.K + TK - 1) / TK * TK;
   const int kseg = k_pad / TK, kk = OZ_S * k_pad;
   const int nk = std::max(1, std::min(64, ex.emu_chunk));
   const int nsplit = oz_splits(kseg, nk);
+  CC_REQUIRE(k_pad < (1 << 24), CC_ERR_INVALID, "FP64-emulated contraction: sum longer than 2^24");
+  const bool onchip = oz_onchip(ex, g, kseg, nsplit);
+  const int tn = onchip ? OZ_TN : TN;
+  const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + tn - 1) / tn * tn;
   auto blocks_for_rows = [&](size_t rows) {
     return (int)std::max<size_t>(1, std::min<size_t>((rows + 7) / 8, (size_t)ex.sm_count * 16));
   };
@@ -1112,7 +1519,41 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   stage(g.B, g.bn, g.bk, g.bb, g.N, rowsB, 1, eB, fB);
   CC_CUDA(cudaGetLastError());
   CUtensorMap mA = make_map(fA, kk, rowsA, g.batch, TM, true);
-  CUtensorMap mB = make_map(fB, kk, rowsB, g.batch, TN, true);
+  CUtensorMap mB = make_map(fB, kk, rowsB, g.batch, tn, true);
+  if (onchip) {
+    OzArgs o{};
+    o.M = g.M;
+    o.N = g.N;
+    o.num_m = rowsA / TM;
+    o.num_n = rowsB / OZ_TN;
+    o.batch = g.batch;
+    o.m_fast = o.num_m <= o.num_n ? 1 : 0;
+    const long long tiles = (long long)o.num_m * o.num_n * g.batch;
+    CC_REQUIRE(tiles < (1LL << 31), CC_ERR_INVALID, "FP64-emulated contraction: too many tiles");
+    o.tiles = (int)tiles;
+    o.kseg = kseg;
+    o.nk = nk;
+    o.nsplit = nsplit;
+    o.cm = g.cm;
+    o.cn = g.cn;
+    o.cb = g.cb;
+    o.alpha = g.alpha;
+    o.beta = g.beta;
+    o.C = g.C;
+    o.expA = eA;
+    o.expB = eB;
+    o.rowsA_pad = rowsA;
+    o.rowsB_pad = rowsB;
+    o.err = ex.dev_flag;
+    o.wait_ns = ex.wait_ns;
+    static std::atomic<uint64_t> attr_done{0};
+    ensure_smem_attr(oz_gemm_kernel, attr_done, OZ_SMEM_BYTES);
+    oz_gemm_kernel<<<(int)std::min<long long>(tiles, ex.sm_count), THREADS, OZ_SMEM_BYTES, ex.stream>>>(mA, mB, o);
+    ex.count();
+    CC_CUDA(cudaGetLastError());
+    if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
+    return;
+  }
   TcArgs a{};
   a.M = g.M;
   a.N = g.N;
@@ -1147,17 +1588,11 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   job.a = a;
   TcJob<true>* one = &job;
   tc_launch_group<true, EPI_PART, 1>(ex, &one, 1);
-  // the fixed-point sum's bound: the level-L chunk sums add up to (L - 1) k_pad (2^beta - 1)^2
-  double bound = 0.0;
-  for (int L = 2; L <= OZ_S + 1; ++L)
-    bound += (L - 1) * (double)k_pad * (double)((1 << OZ_BETA) - 1) * ((1 << OZ_BETA) - 1) *
-             std::ldexp(1.0, OZ_BETA * (OZ_S + 1 - L));
-  const int gsh = std::max(0, (int)std::ceil(std::log2(bound)) - 61);
   const size_t rows = (size_t)g.batch * g.M;
   const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
   const size_t items = rows * ((g.N + piece - 1) / piece);
   const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
-  oz_combine_kernel<<<rblocks, 256, 0, ex.stream>>>(g, a.part, kseg, nk, gsh, eA, rowsA, eB, rowsB, piece);
+  oz_combine_kernel<<<rblocks, 256, 0, ex.stream>>>(g, a.part, kseg, nk, eA, rowsA, eB, rowsB, piece);
   ex.count();
   CC_CUDA(cudaGetLastError());
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
@@ -1168,6 +1603,26 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
 void k_wait_selftest(const Exec& ex) {
   CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "the wait self-test needs a device error flag");
   wait_selftest_kernel<<<1, 32, 0, ex.stream>>>(ex.dev_flag, ex.wait_ns);
+  ex.count();
+  CC_CUDA(cudaGetLastError());
+}
+
+void k_ladder_pm_stage(const Exec& ex, bool bf, int nseg, long long rows, int v, const float* W, void* Wp,
+                       long long kpP, void* Wm, long long kpQ) {
+  CC_REQUIRE(nseg == 1 || nseg == 3, CC_ERR_INVALID, "ladder split: one or three staging segments");
+  const long long Pv = (long long)v * (v + 1) / 2, Qv = (long long)v * (v - 1) / 2;
+  CC_REQUIRE(kpP >= Pv && kpP - Pv < 64 && (!Wm || (kpQ >= Qv && kpQ - Qv < 64)), CC_ERR_INVALID,
+             "ladder split: k padding");
+  const int nt = (v + 31) / 32;
+  const long long items = rows * (long long)(nt * (nt + 1) / 2);
+  if (items <= 0) return;
+  const int blocks = (int)std::min<long long>(items, (long long)ex.sm_count * 8);
+  if (bf)
+    ladder_pm_stage_kernel<__nv_bfloat16><<<blocks, 256, 0, ex.stream>>>(
+        rows, v, W, static_cast<__nv_bfloat16*>(Wp), kpP, static_cast<__nv_bfloat16*>(Wm), kpQ, nseg);
+  else
+    ladder_pm_stage_kernel<float><<<blocks, 256, 0, ex.stream>>>(rows, v, W, static_cast<float*>(Wp), kpP,
+                                                                static_cast<float*>(Wm), kpQ, nseg);
   ex.count();
   CC_CUDA(cudaGetLastError());
 }

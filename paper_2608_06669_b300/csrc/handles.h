@@ -24,6 +24,8 @@ struct cc_ctx {
   long long stage_cap = -1;                    // CC_OPT_STAGE_CACHE_BYTES (-1: the default)
   int graphs = 1;                              // CC_OPT_GRAPHS
   int emu_chunk = 64;                          // CC_OPT_EMU_CHUNK
+  int ladder_pack = -1;                        // CC_OPT_LADDER_PACK
+  int emu_onchip = -1;                         // CC_OPT_EMU_ONCHIP
   ccpnk::Exec ex() {
     ccpnk::Exec e;
     e.stream = stream;
@@ -37,6 +39,8 @@ struct cc_ctx {
     e.stage_cap = stage_cap;
     e.graphs = graphs;
     e.emu_chunk = emu_chunk;
+    e.ladder_pack = ladder_pack;
+    e.emu_onchip = emu_onchip;
     return e;
   }
 };

@@ -365,17 +365,20 @@ def test_pnk_with_emulated_outer_residual(ctx, prec):
 
 
 @pytest.mark.parametrize("chunk", [16, 64])
-def test_fp64_emulation_chunk_sums_at_their_bound(ctx, chunk):
-    """Worst case for the exactness of the emulation's FP32 chunk sums: every entry of B is
-    1 - 2^-48, so every digit slice of the ladder build's operands holds the largest digit (63)
-    and a chunk of 64 (or 16) k blocks sums 4096 (1024) products 63 * 63 = 16,257,024 (4,064,256),
-    just below 2^24 (2^22). The emulated residual must still equal the native FP64 one."""
+@pytest.mark.parametrize("bits", [54, 56])
+def test_fp64_emulation_chunk_sums_at_their_bound(ctx, chunk, bits):
+    """Worst cases for the exactness of the emulation's FP32 chunk sums. With every entry of B
+    equal to 1 - 2^-54, every digit slice of the ladder build's operands holds the largest digit
+    (63: nine slices of six bits) and a chunk of 64 (or 16) k blocks sums 4096 (1024) products
+    63 * 63 = 16,257,024 (4,064,256), just below 2^24 (2^22). With 1 - 2^-56 the rounding to 54
+    bits carries into the leading digit (64, the rest 0): the leading level's chunk sums reach
+    4096 * 64 * 64 = 2^24 exactly. The emulated residual must still equal the native FP64 one."""
     from paper_2608_06669_b300 import ccpnk
 
     o, v, naux = 1, 40, 640
     n = o + v
     fock = np.diag(np.concatenate([[-1.0], np.linspace(0.5, 2.0, v)]))
-    B = np.full((naux, n, n), 1.0 - 2.0 ** -48)
+    B = np.full((naux, n, n), 1.0 - 2.0 ** -bits)
     g = ccpnk.System(ctx, o, v, naux, fock, B)
     # t1 = 0 leaves the dressed factor equal to B, so the ladder build's operands keep the digits
     _, t2 = synth.random_amplitudes(np.random.default_rng(5), o, v, 0.01, 0.01)
