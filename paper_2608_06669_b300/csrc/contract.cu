@@ -61,12 +61,18 @@ __device__ __forceinline__ long long cidx(const CIdx& c, int x) {
 // TMR x TNR outputs per thread on a 16 x 16 thread grid: a (16 TMR) x (16 TNR) tile. FP64 on
 // this part is so much slower than its loads and shared memory that even the smallest tile is
 // bound by the FMA pipe, so the host picks the tile that wastes the least on padding and
-// spreads the work most evenly over the SMs.
-template <int TMR, int TNR>
-__global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
+// spreads the work most evenly over the SMs. Acc = float is the same kernel on the FP32 pipe
+// (FP64 operands rounded to FP32 as they are staged, FP64 output and split-k partials): the
+// thin contractions of the tensor-core precisions, whose tiles the tensor cores would mostly
+// pad, with at most 512 terms summed in FP32 per split.
+__device__ __forceinline__ double fma_acc(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_acc(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <int TMR, int TNR, typename Acc>
+__device__ __forceinline__ void gemm_fma_body(const GemmArgs& g) {
   constexpr int TBM = 16 * TMR, TBN = 16 * TNR;
-  __shared__ double As[BK][TBM + 1];
-  __shared__ double Bs[BK][TBN + 1];
+  __shared__ Acc As[BK][TBM + 1];
+  __shared__ Acc Bs[BK][TBN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
@@ -98,27 +104,27 @@ __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
   for (int bz = blockIdx.z / g.splits; bz < g.batch; bz += gridDim.z / g.splits) {
     const double* A = g.A + cidx(g.ab, bz);
     const double* B = g.B + cidx(g.bb, bz);
-    double acc[TMR][TNR];
+    Acc acc[TMR][TNR];
 #pragma unroll
     for (int i = 0; i < TMR; ++i)
 #pragma unroll
-      for (int j = 0; j < TNR; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < TNR; ++j) acc[i][j] = Acc(0);
 
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
       for (int r = 0; r < TMR; ++r) {
         int k = k0 + a_kk[r];
-        As[a_kk[r]][a_mm[r]] = (a_moff[r] >= 0 && k < kend) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0;
+        As[a_kk[r]][a_mm[r]] = (Acc)((a_moff[r] >= 0 && k < kend) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0);
       }
 #pragma unroll
       for (int r = 0; r < TNR; ++r) {
         int kb = k0 + b_kk[r];
-        Bs[b_kk[r]][b_nn[r]] = (b_noff[r] >= 0 && kb < kend) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0;
+        Bs[b_kk[r]][b_nn[r]] = (Acc)((b_noff[r] >= 0 && kb < kend) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double a[TMR], b[TNR];
+        Acc a[TMR], b[TNR];
 #pragma unroll
         for (int i = 0; i < TMR; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
 #pragma unroll
         for (int i = 0; i < TMR; ++i)
 #pragma unroll
-          for (int j = 0; j < TNR; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < TNR; ++j) acc[i][j] = fma_acc(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
 #pragma unroll
         for (int j = 0; j < TNR; ++j) {
           int n = n0 + tx + 16 * j;
-          if (n < g.N) P[(size_t)m * g.N + n] = acc[i][j];
+          if (n < g.N) P[(size_t)m * g.N + n] = (double)acc[i][j];
         }
       }
       continue;
@@ -156,12 +162,21 @@ __global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
         int n = n0 + tx + 16 * j;
         if (n >= g.N) continue;
         double* c = C + cm + cidx(g.cn, n);
-        double val = g.alpha * acc[i][j];
+        double val = g.alpha * (double)acc[i][j];
         if (g.beta != 0.0) val = fma(g.beta, *c, val);
         *c = val;
       }
     }
   }
+}
+
+template <int TMR, int TNR>
+__global__ void __launch_bounds__(NT, 2) gemm_f64_kernel(GemmArgs g) {
+  gemm_fma_body<TMR, TNR, double>(g);
+}
+template <int TMR, int TNR>
+__global__ void __launch_bounds__(NT, 2) gemm_f32_kernel(GemmArgs g) {
+  gemm_fma_body<TMR, TNR, float>(g);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,7 +426,8 @@ long long inner_stride(const CIdx& c) { return (c.e1 == 1 && c.e2 == 1) ? c.s0 :
 
 // A contraction too thin for 128 x 256 tensor-core tiles (a short k, or a narrow M or N) costs
 // more in staging, padding and launch latency than it saves: true when the tensor-core run is
-// estimated to be faster than the FP64 kernel (which is more accurate, never less).
+// estimated to be faster than the CUDA-core kernel (FP32 pipe for the single-precision kinds,
+// FP64 pipe for the FP64 emulation; either is at least as accurate).
 bool tc_faster(const Exec& ex, cc_precision prec, const GemmArgs& g) {
   const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
   const int tk = prec == CC_MIXED_BF16X3 || prec == CC_FP64_EMU ? 64 : 32;
@@ -426,10 +442,14 @@ bool tc_faster(const Exec& ex, cc_precision prec, const GemmArgs& g) {
     t_tc = 20e-6 + kOzProducts * padded / 1.2e15 + chunks * 8.0 * g.M * (double)g.N * g.batch / 5e12 +
            ((double)g.M + g.N) * kp * g.batch * (8.0 + 2.0 * kOzSlices) / 5e12;
   }
-  // the FP64 kernel's parallelism: 16 x 16 tiles, k split at most 64 ways
-  const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch * std::min(64, std::max(1, g.K / 32));
+  // the CUDA-core kernel's parallelism: 16 x 16 tiles, k split at most 64 ways (FP64) or 1024 (FP32)
+  const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch *
+                        std::min(prec == CC_FP64_EMU ? 64 : 1024, std::max(1, g.K / 32));
   const double flops16 = 2.0 * ((g.M + 15) / 16 * 16.0) * ((g.N + 15) / 16 * 16.0) * g.K * g.batch;
-  double t_f64 = 4e-6 + flops16 / (1.0e12 * std::min(1.0, blocks / ex.sm_count));
+  // FP64 pipe, or the FP32 kernel as measured on these shapes (its staging loads and compound
+  // indices, not the FP32 pipe's 75 TFLOP/s, set its pace)
+  const double cuda_rate = prec == CC_FP64_EMU ? 1.0e12 : 5.0e12;
+  double t_f64 = 4e-6 + flops16 / (cuda_rate * std::min(1.0, blocks / ex.sm_count));
   if ((g.N == 1 || g.M == 1) && (long long)(g.N == 1 ? g.M : g.N) * g.batch >= 256)
     t_f64 = 4e-6 + 8.0 * (g.N == 1 ? g.M : g.N) * (double)g.K * g.batch / 2e12;  // the FP64 GEMV reads the matrix once
   return t_tc <= t_f64;
@@ -438,11 +458,15 @@ bool tc_faster(const Exec& ex, cc_precision prec, const GemmArgs& g) {
 void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   CC_REQUIRE(!((g.so || g.sb) && (prec == CC_FP64 || prec == CC_DF64)), CC_ERR_INVALID, "staged operands need a tensor-core precision");
+  // thin contractions of the single-precision tensor-core kinds run on the FP32 pipe (more
+  // accurate than their tensor-core passes); those of the FP64 emulation on the FP64 pipe
+  bool f32 = false;
   if (prec != CC_FP64 && prec != CC_DF64) {
     if (g.so || g.sb || tc_faster(ex, prec, g)) {
       gemm_tc(ex, prec, g, tag);
       return;
     }
+    f32 = prec != CC_FP64_EMU;
     prec = CC_FP64;
   }
   // (a few outputs over a long k stay on the split-k GEMM path, which spreads k over SMs)
@@ -459,6 +483,19 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
     if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
     return;
   }
+  // The kernel's lanes run along the columns of C; when C is contiguous along its rows instead
+  // (and strided along its columns), the transposed product C^T = B A^T writes the same memory
+  // with coalesced stores. Each output is the same k-ordered sum either way.
+  if (inner_stride(g.cn) != 1 && inner_stride(g.cm) == 1) {
+    std::swap(g.M, g.N);
+    std::swap(g.A, g.B);
+    std::swap(g.am, g.bn);
+    std::swap(g.ak, g.bk);
+    std::swap(g.ab, g.bb);
+    std::swap(g.cm, g.cn);
+    g.a_kfast = g.K <= 0 || inner_stride(g.ak) == 1;
+    g.b_kfast = g.K <= 0 || (inner_stride(g.bk) == 1 && inner_stride(g.bn) != 1);
+  }
   const int ksteps = (g.K + BK - 1) / BK;
   // FP64: tile (16 TMR) x (16 TNR) and split-K factor from a model of the FMA-bound kernel:
   // blocks are spread evenly over the SMs, so the time is ceil(blocks / SMs) blocks' FMA
@@ -467,17 +504,21 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
   // The double-float kernel keeps its 64 x 64 tile and the occupancy-based split.
   int tmr = 4, tnr = 4, splits = 1;
   if (prec == CC_FP64) {
-    const double fma_rate = 2.0 * 2.0e9;  // FP64 FMAs per second of one SM
+    // FP64 FMAs per second of one SM; the FP32 kernel runs about 4x that (measured), bound by
+    // its staging loads rather than by the FP32 pipe
+    const double fma_rate = 2.0 * 2.0e9 * (f32 ? 4.0 : 1.0);
     const double blk_cost = 2e-6, hbm = 6.0e12;
     double best = 1e300;
-    const int smax = std::max(1, std::min(64, ksteps / 2));
+    // in FP32 at most 32 k steps of 16 (512 terms) per split
+    const int smin = f32 ? (ksteps + 31) / 32 : 1;
+    const int smax = std::max(smin, std::min(f32 ? 1024 : 64, ksteps / 2));
     for (int r : {4, 2, 1})
       for (int c : {4, 2, 1}) {
         const long long bm = 16 * r, bn = 16 * c;
         const long long tiles = ((g.M + bm - 1) / bm) * ((g.N + bn - 1) / bn) * g.batch;
         if ((g.M + bm - 1) / bm > 65535) continue;
-        for (int sp = 1; sp <= smax; ++sp) {
-          if (sp > 1 && tiles * sp > 16LL * ex.sm_count * 8) break;  // enough blocks already
+        for (int sp = smin; sp <= smax; ++sp) {
+          if (sp > smin && tiles * sp > 16LL * ex.sm_count * 8) break;  // enough blocks already
           const long long kst = (ksteps + sp - 1) / sp;
           const double per_sm = (double)((tiles * sp + ex.sm_count - 1) / ex.sm_count);
           double t = per_sm * ((double)bm * bn * BK * kst / fma_rate + blk_cost);
@@ -510,6 +551,12 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
   if (ex.timing(tag)) ex.mark_begin(&ev);
   if (prec == CC_DF64) {
     gemm_df64_kernel<<<grid, NT, 0, ex.stream>>>(g);
+  } else if (f32) {
+    auto k = gemm_f32_kernel<4, 4>;
+    if (tmr == 4) k = tnr == 4 ? gemm_f32_kernel<4, 4> : tnr == 2 ? gemm_f32_kernel<4, 2> : gemm_f32_kernel<4, 1>;
+    else if (tmr == 2) k = tnr == 4 ? gemm_f32_kernel<2, 4> : tnr == 2 ? gemm_f32_kernel<2, 2> : gemm_f32_kernel<2, 1>;
+    else k = tnr == 4 ? gemm_f32_kernel<1, 4> : tnr == 2 ? gemm_f32_kernel<1, 2> : gemm_f32_kernel<1, 1>;
+    k<<<grid, NT, 0, ex.stream>>>(g);
   } else {
     auto k = gemm_f64_kernel<4, 4>;
     if (tmr == 4) k = tnr == 4 ? gemm_f64_kernel<4, 4> : tnr == 2 ? gemm_f64_kernel<4, 2> : gemm_f64_kernel<4, 1>;

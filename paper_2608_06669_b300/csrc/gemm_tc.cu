@@ -1459,20 +1459,18 @@ int oz_splits(int kseg, int nk) {
 
 // Which form of the emulated product runs: on chip (oz_gemm_kernel: 128 x 128 tiles, every slice
 // product of a tile on one SM, no partial sums) or through FP32 partial sums (every (level, chunk)
-// slice product of a 128 x 256 tile a split of its own, then oz_combine_kernel). The first moves
-// 8 bytes less per output and slice product but spreads only the output tiles over the SMs;
-// a time model of both decides.
-bool oz_onchip(const Exec& ex, const GemmArgs& g, int kseg, int nsplit) {
+// slice product of a 128 x 256 tile a split of its own, then oz_combine_kernel). On chip saves 8
+// bytes per output and chunk but feeds the tensor cores from L2 at twice the bytes per MMA of
+// the wider tiles (measured: about 0.44 of the BF16 peak against 0.56 with partial sums on an
+// 8100^3 product at o = 30, v = 270), and spreads only the output tiles over the SMs. So it
+// runs where the partial sums weigh most against the MMA work, short sums: measured on the
+// o = 10, 20 and 30 workloads, it wins for k up to 16 blocks of 64 (the ladder build over the
+// auxiliary index, 10-20% faster) and loses beyond (the rings and the ladder contraction over
+// o v and v^2), given at least one tile per SM.
+bool oz_onchip(const Exec& ex, const GemmArgs& g, int kseg) {
   if (ex.emu_onchip >= 0) return ex.emu_onchip == 1;
-  const double sms = ex.sm_count, rate = 1.6e13, hbm = 6e12;  // BF16 MMA flop/s of one SM; HBM B/s
-  const double kblocks = (double)kOzProducts * kseg;             // k blocks of a tile's slice products
-  const double t128 = 2.0 * TM * OZ_TN * 64.0 * kblocks / rate + 2e-6;
   const double tiles128 = (double)g.batch * std::ceil(g.M / (double)TM) * std::ceil(g.N / (double)OZ_TN);
-  const double onchip = std::ceil(tiles128 / sms) * t128;
-  const double tiles256 = (double)g.batch * std::ceil(g.M / (double)TM) * std::ceil(g.N / (double)TN);
-  const double tsplit = 2.0 * TM * TN * 64.0 * kblocks / nsplit / rate + 1e-6;
-  const double parts = std::ceil(tiles256 * nsplit / sms) * tsplit + 8.0 * nsplit * g.batch * g.M * (double)g.N / hbm + 5e-6;
-  return onchip < parts;
+  return kseg <= 16 && tiles128 >= ex.sm_count;
 }
 
 void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
@@ -1482,7 +1480,7 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   const int nk = std::max(1, std::min(64, ex.emu_chunk));
   const int nsplit = oz_splits(kseg, nk);
   CC_REQUIRE(k_pad < (1 << 24), CC_ERR_INVALID, "FP64-emulated contraction: sum longer than 2^24");
-  const bool onchip = oz_onchip(ex, g, kseg, nsplit);
+  const bool onchip = oz_onchip(ex, g, kseg);
   const int tn = onchip ? OZ_TN : TN;
   const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + tn - 1) / tn * tn;
   auto blocks_for_rows = [&](size_t rows) {
