@@ -865,9 +865,11 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 // level. The MMA thread alternates two FP32 accumulators over a tile's slice products; the
 // epilogue warps read each exact chunk sum once and add it, shifted for its level, into a 64-bit
 // fixed-point sum in registers (64 columns of one row per thread), so no partial sum leaves the
-// SM. After the last level of the first group (oz_fixed_value) the register sums go to TMEM and
-// the second group starts from zero; the two are joined at the end. Same integers, same single
-// rounding as oz_combine_kernel: the result is the same bits.
+// SM. A tile's slice products run from the highest level down: the longest ones come first, so
+// while the epilogue finishes one tile (conversion and stores) the MMA thread works through the
+// next tile's two longest products. After the levels above OZ_LH (oz_fixed_value) the register
+// sums are parked in TMEM and the levels up to OZ_LH start from zero; the two are joined at the
+// end. Same integers, same single rounding as oz_combine_kernel: the result is the same bits.
 // ---------------------------------------------------------------------------
 constexpr int OZ_TN = 128;
 constexpr int OZ_STAGES = 5;
@@ -983,9 +985,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
         int bz, m0, n0;
         oz_tile(a, t, bz, m0, n0);
-        for (int sp = 0; sp < a.nsplit && ok; ++sp) {
+        for (int i = 0; i < a.nsplit && ok; ++i) {
           int kA0, kB0, nkb;
-          oz_split_range(OZ_S, a.kseg, a.nk, sp, kA0, kB0, nkb);
+          oz_split_range(OZ_S, a.kseg, a.nk, a.nsplit - 1 - i, kA0, kB0, nkb);
           for (int kb = 0; kb < nkb; ++kb, ++q) {
             const int s = q % OZ_STAGES;
             const uint32_t ph = (q / OZ_STAGES) & 1;
@@ -1004,13 +1006,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       uint32_t q = 0, u = 0;  // pipeline slots; slice products (accumulator uses)
       for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
-        for (int sp = 0; sp < a.nsplit; ++sp, ++u) {
+        for (int i = 0; i < a.nsplit; ++i, ++u) {
           const int acc = u & 1;
           if (!mbar_wait(tempty0 + 8 * acc, ((u >> 1) & 1) ^ 1, wait_ns)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t d = tmem + (uint32_t)(acc * OZ_TN);
           int kA0, kB0, nkb;
-          oz_split_range(OZ_S, a.kseg, a.nk, sp, kA0, kB0, nkb);
+          oz_split_range(OZ_S, a.kseg, a.nk, a.nsplit - 1 - i, kA0, kB0, nkb);
           for (int kb = 0; kb < nkb; ++kb, ++q) {
             const int s = q % OZ_STAGES;
             if (!mbar_wait(full0 + 8 * s, (q / OZ_STAGES) & 1, wait_ns)) { ok = false; break; }
@@ -1040,7 +1042,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int half = (warp - 2) >> 2;  // columns half * 64 .. + 63 of the tile
     double* tile = ep + (warp - 2) * OZ_EP_DOUBLES;
     const uint32_t lanes = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t thigh = lanes + 2 * OZ_TN + half * 128;  // the first group's sums: 64 int64
+    const uint32_t tpark = lanes + 2 * OZ_TN + half * 128;  // the first group's sums: 64 int64
     uint32_t u = 0;
     for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
       int bz, m0, n0;
@@ -1048,11 +1050,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       long long acc[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) acc[j] = 0;
-      bool high = true;  // summing the first group of levels
-      for (int sp = 0; sp < a.nsplit; ++sp, ++u) {
+      bool low = true;  // summing the levels above OZ_LH (they come first)
+      for (int i = 0; i < a.nsplit; ++i, ++u) {
         int kA0, kB0, nkb;
-        const int L = oz_split_range(OZ_S, a.kseg, a.nk, sp, kA0, kB0, nkb);
-        if (high && L > OZ_LH) {  // first group done: park its sums in TMEM, start the second
+        const int L = oz_split_range(OZ_S, a.kseg, a.nk, a.nsplit - 1 - i, kA0, kB0, nkb);
+        if (low && L <= OZ_LH) {  // first group done: park its sums in TMEM, start the second
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
             uint32_t w[16];
@@ -1061,12 +1063,12 @@ __global__ void __launch_bounds__(THREADS, 1)
               w[2 * j] = (uint32_t)(unsigned long long)acc[p * 8 + j];
               w[2 * j + 1] = (uint32_t)((unsigned long long)acc[p * 8 + j] >> 32);
             }
-            tmem_st16(thigh + p * 16, w);
+            tmem_st16(tpark + p * 16, w);
           }
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int j = 0; j < 64; ++j) acc[j] = 0;
-          high = false;
+          low = false;
         }
         const int sh = oz_level_shift(L);
         const int buf = u & 1;
@@ -1104,15 +1106,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int c0 = n0 + half * 64 + p * 16;
         if (!rows_left || c0 >= a.N) break;  // warp-uniform
         uint32_t w0[16], w1[16];
-        tmem_ld16(thigh + p * 32, w0);
-        tmem_ld16(thigh + p * 32 + 16, w1);
+        tmem_ld16(tpark + p * 32, w0);
+        tmem_ld16(tpark + p * 32 + 16, w1);
         tmem_wait_ld(w0, w1);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const uint32_t lo32 = j < 8 ? w0[2 * j] : w1[2 * (j - 8)];
           const uint32_t hi32 = j < 8 ? w0[2 * j + 1] : w1[2 * (j - 8) + 1];
-          const long long acc_h = (long long)(((unsigned long long)hi32 << 32) | lo32);
-          tile[lane * 17 + j] = oz_fixed_value(acc_h, acc[p * 16 + j]);
+          const long long acc_l = (long long)(((unsigned long long)hi32 << 32) | lo32);  // parked
+          tile[lane * 17 + j] = oz_fixed_value(acc[p * 16 + j], acc_l);
         }
         __syncwarp();
         const int col = c0 + (lane & 15);
