@@ -442,9 +442,8 @@ bool tc_faster(const Exec& ex, cc_precision prec, const GemmArgs& g) {
     t_tc = 20e-6 + kOzProducts * padded / 1.2e15 + chunks * 8.0 * g.M * (double)g.N * g.batch / 5e12 +
            ((double)g.M + g.N) * kp * g.batch * (8.0 + 2.0 * kOzSlices) / 5e12;
   }
-  // the CUDA-core kernel's parallelism: 16 x 16 tiles, k split at most 64 ways (FP64) or 1024 (FP32)
-  const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch *
-                        std::min(prec == CC_FP64_EMU ? 64 : 1024, std::max(1, g.K / 32));
+  // the CUDA-core kernel's parallelism: 16 x 16 tiles, k split at most 1024 ways
+  const double blocks = (double)((g.M + 15) / 16) * ((g.N + 15) / 16) * g.batch * std::min(1024, std::max(1, g.K / 32));
   const double flops16 = 2.0 * ((g.M + 15) / 16 * 16.0) * ((g.N + 15) / 16 * 16.0) * g.K * g.batch;
   // FP64 pipe, or the FP32 kernel as measured on these shapes (its staging loads and compound
   // indices, not the FP32 pipe's 75 TFLOP/s, set its pace)
@@ -511,7 +510,7 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
     double best = 1e300;
     // in FP32 at most 32 k steps of 16 (512 terms) per split
     const int smin = f32 ? (ksteps + 31) / 32 : 1;
-    const int smax = std::max(smin, std::min(f32 ? 1024 : 64, ksteps / 2));
+    const int smax = std::max(smin, std::min(1024, ksteps / 2));
     for (int r : {4, 2, 1})
       for (int c : {4, 2, 1}) {
         const long long bm = 16 * r, bn = 16 * c;

@@ -719,6 +719,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     if (lane == 0) {
       uint32_t q = 0;
       int it = 0, p = 0;
+      const uint64_t descA = sdesc(smem_u32(sA)), descB = sdesc(smem_u32(sB));
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
         const int acc = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
@@ -733,10 +734,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
           const uint32_t ph = (q / STAGES) & 1;
           if (!mbar_wait(full0 + 8 * s, ph, wait_ns)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+          // the descriptors' address field counts 16 bytes: stage s and step j (UK elements = 32
+          // bytes) are offsets from the first stage's descriptors
+          const uint64_t da0 = descA + (uint64_t)(s * (A_BYTES >> 4)), db0 = descB + (uint64_t)(s * (B_BYTES >> 4));
 #pragma unroll
           for (int j = 0; j < TK / UK; ++j) {
-            const uint64_t da = sdesc(a0 + j * 32), db = sdesc(b0 + j * 32);  // UK elements = 32 bytes
+            const uint64_t da = da0 + 2 * j, db = db0 + 2 * j;
             const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
             if constexpr (BF) {
               asm volatile(
@@ -1005,6 +1008,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       uint32_t q = 0, u = 0;  // pipeline slots; slice products (accumulator uses)
+      const uint64_t descA = sdesc(smem_u32(sA)), descB = sdesc(smem_u32(sB));
       for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
         for (int i = 0; i < a.nsplit; ++i, ++u) {
           const int acc = u & 1;
@@ -1017,10 +1021,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int s = q % OZ_STAGES;
             if (!mbar_wait(full0 + 8 * s, (q / OZ_STAGES) & 1, wait_ns)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * OZ_B_BYTES);
+            const uint64_t da0 = descA + (uint64_t)(s * (A_BYTES >> 4)), db0 = descB + (uint64_t)(s * (OZ_B_BYTES >> 4));
 #pragma unroll
             for (int j = 0; j < TK / UK; ++j) {
-              const uint64_t da = sdesc(a0 + j * 32), db = sdesc(b0 + j * 32);
+              const uint64_t da = da0 + 2 * j, db = db0 + 2 * j;
               const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
