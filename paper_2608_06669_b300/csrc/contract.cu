@@ -110,18 +110,29 @@ __device__ __forceinline__ void gemm_fma_body(const GemmArgs& g) {
 #pragma unroll
       for (int j = 0; j < TNR; ++j) acc[i][j] = Acc(0);
 
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    // the next k slice is loaded into registers while the current one is multiplied, so the
+    // loads' latency hides behind the FMAs
+    Acc ra[TMR], rb[TNR];
+    auto load_slice = [&](int k0) {
 #pragma unroll
       for (int r = 0; r < TMR; ++r) {
-        int k = k0 + a_kk[r];
-        As[a_kk[r]][a_mm[r]] = (Acc)((a_moff[r] >= 0 && k < kend) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0);
+        const int k = k0 + a_kk[r];
+        ra[r] = (Acc)((a_moff[r] >= 0 && k < kend) ? A[a_moff[r] + cidx(g.ak, k)] : 0.0);
       }
 #pragma unroll
       for (int r = 0; r < TNR; ++r) {
-        int kb = k0 + b_kk[r];
-        Bs[b_kk[r]][b_nn[r]] = (Acc)((b_noff[r] >= 0 && kb < kend) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0);
+        const int kb = k0 + b_kk[r];
+        rb[r] = (Acc)((b_noff[r] >= 0 && kb < kend) ? B[b_noff[r] + cidx(g.bk, kb)] : 0.0);
       }
+    };
+    if (kbeg < kend) load_slice(kbeg);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < TMR; ++r) As[a_kk[r]][a_mm[r]] = ra[r];
+#pragma unroll
+      for (int r = 0; r < TNR; ++r) Bs[b_kk[r]][b_nn[r]] = rb[r];
       __syncthreads();
+      if (k0 + BK < kend) load_slice(k0 + BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         Acc a[TMR], b[TNR];
