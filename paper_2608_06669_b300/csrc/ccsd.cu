@@ -82,6 +82,8 @@ bool ladder_pack_pays(int o, int v, cc_precision prec) {
   return packed < plain;
 }
 
+constexpr size_t kLadderGroupBytes = (size_t)3 << 29;  // 1.5 GiB of staged slabs at once
+
 int ladder_block_for(int v) {
   const double cap = 2.0 * 1024 * 1024 * 1024;
   const double per_a = 8.0 * (double)v * v * v;
@@ -179,11 +181,23 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
   const int Po = o * (o + 1) / 2, Qo = o * (o - 1) / 2, Pv = v * (v + 1) / 2, Qv = v * (v - 1) / 2;
   const long long kpP = ((long long)Pv + align - 1) / align * align, kpQ = ((long long)Qv + align - 1) / align * align;
   const size_t esz = bf ? 2 : 4;
+  // Tensor cores without the split: when the slabs of all blocks of a fit side by side in the
+  // staging budget, one grouped launch builds them all and one more contracts them all (the
+  // contractions of a small problem fill the SMs together, not one by one)
+  const int blk = ladder_block_;
+  size_t group_rows = 0;
+  for (int a0 = 0; a0 < v; a0 += blk) group_rows += ((size_t)std::min(blk, v - a0) * (v - a0) + 255) / 256 * 256;
+  const bool grouped = tensor && !pack && group_rows * (size_t)kk * esz <= kLadderGroupBytes;
   if (tensor) {
     // the larger of the two paddings, and room for the two pair layouts (each padded)
     const long long kmax = ((long long)v * v + 63) / 64 * 64 + 128;
-    if (!W2_.p) W2_.alloc(ex_.pool, ((size_t)rows_pad * 3 * kmax * 4 + 7) / 8);
-    const int mode = (int)prec + (pack ? 16 : 0);
+    size_t need = (size_t)rows_pad * 3 * kmax * 4;
+    if (grouped) need = std::max(need, group_rows * (size_t)kk * esz);
+    if (W2_.n * sizeof(double) < need) {
+      W2_.alloc(ex_.pool, (need + 7) / 8);
+      w2_mode_ = -1;
+    }
+    const int mode = (int)prec + (pack ? 16 : 0) + (grouped ? 32 : 0);
     if (w2_mode_ != mode) {  // the k padding of the plain layout must read as zeros
       CC_CUDA(cudaMemsetAsync(W2_.p, 0, W2_.n * sizeof(double), ex_.stream));
       w2_mode_ = mode;
@@ -203,7 +217,44 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
     Tmn = Tp + (size_t)Po * Pv;
     k_ladder_pm_T(ex_, o, v, T, Tp, Tmn);
   }
-  const int blk = ladder_block_;
+  if (grouped) {
+    std::vector<StagedOut> sos;
+    std::vector<StagedIn> sbs;
+    sos.reserve((v + blk - 1) / blk);
+    sbs.reserve((v + blk - 1) / blk);
+    std::vector<ContractSpec> builds, cons;
+    StageCache tcache;  // the amplitudes staged once for all blocks when they are not kept across calls
+    tcache.cap = ~(size_t)0 >> 1;
+    size_t row0 = 0;
+    for (int a0 = 0; a0 < v; a0 += blk) {
+      const int al = std::min(blk, v - a0), bl = v - a0;
+      const int rp = (al * bl + 255) / 256 * 256;
+      void* base = static_cast<char*>(W2) + row0 * (size_t)kk * esz;
+      row0 += rp;
+      sos.push_back(StagedOut{base, kpad, nseg, nseg == 3 ? 0b010 : 0});
+      sbs.push_back(StagedIn{base, rp, (int)kk});
+      ContractSpec b;
+      b.A = view_strided(X + (size_t)a0 * v, "Pac", {Paux, al, v}, {(long long)v * v, v, 1});
+      b.B = view_strided(Y + (size_t)a0 * v, "Pbd", {Paux, bl, v}, {(long long)v * v, v, 1});
+      b.C = view_strided(nullptr, "abcd", {al, bl, v, v}, {(long long)bl * kk, kk, v, 1});
+      b.cache = &stage_;
+      b.cache_mask = fixed_xy ? 3 : 0;
+      b.so = &sos.back();
+      builds.push_back(b);
+      ContractSpec c;
+      c.A = view(Tm, "ijcd", {o, o, v, v});
+      c.B = view(W_.p, "abcd", {al, bl, v, v});
+      c.C = view_strided(L + (size_t)a0 * v + a0, "ijab", {o, o, al, bl}, {(long long)o * v * v, (long long)v * v, v, 1});
+      c.cache = fixed_t ? &stage_ : &tcache;
+      c.cache_mask = 1;
+      c.sb = &sbs.back();
+      cons.push_back(c);
+    }
+    contract_group(ex_, prec, builds, tb);
+    contract_group(ex_, prec, cons, tc);
+    k_ladder_mirror_add(ex_, o, v, blk, L, R);
+    return;
+  }
   for (int a0 = 0; a0 < v; a0 += blk) {
     const int al = std::min(blk, v - a0);
     const int bl = v - a0;  // b in [a0, v)

@@ -265,7 +265,7 @@ struct GemmArgs {
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag = nullptr);
 // Independent tensor-core GEMMs (no output shared, single-precision kinds) in grouped launches:
 // every problem's tiles in one persistent launch of up to 16 problems per output mode.
-void gemm_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs);
+void gemm_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs, const char* tag = nullptr);
 // One kernel whose bounded wait on an mbarrier that nothing arrives at gives up after
 // ex.wait_ns and sets the device error flag (the self-test of the bounded waits).
 void k_wait_selftest(const Exec& ex);
@@ -306,10 +306,14 @@ struct ContractSpec {
   TView A, B, C;
   StageCache* cache = nullptr;
   int cache_mask = 0;
+  const StagedOut* so = nullptr;  // tensor-core only: C written in staging layout
+  const StagedIn* sb = nullptr;   // tensor-core only: B already staged
 };
 // Independent contractions at one precision: those the tensor cores run best share grouped
-// launches (one persistent launch over all their tiles), the rest run one by one.
-void contract_group(const Exec& ex, cc_precision prec, const std::vector<ContractSpec>& specs);
+// launches (one persistent launch over all their tiles), the rest run one by one. Specs with a
+// staged operand always run on the tensor cores. tag: kernel-timer tag of the whole group.
+void contract_group(const Exec& ex, cc_precision prec, const std::vector<ContractSpec>& specs,
+                    const char* tag = nullptr);
 
 // ---------------------------------------------------------------------------
 // kernels with host launchers (elementwise.cu)

@@ -732,19 +732,20 @@ void contract(const Exec& ex, cc_precision prec, double alpha, const TView& A, c
   for (const GemmArgs& g : plan_contract(alpha, A, B, beta, C, so, sb, cache, cache_mask)) launch_gemm(ex, prec, g, tag);
 }
 
-void contract_group(const Exec& ex, cc_precision prec, const std::vector<ContractSpec>& specs) {
+void contract_group(const Exec& ex, cc_precision prec, const std::vector<ContractSpec>& specs, const char* tag) {
   const bool tc = prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3;
   std::vector<GemmArgs> grouped;
   for (const ContractSpec& c : specs) {
-    std::vector<GemmArgs> gs = plan_contract(c.alpha, c.A, c.B, c.beta, c.C, nullptr, nullptr, c.cache, c.cache_mask);
+    CC_REQUIRE(tc || (!c.so && !c.sb), CC_ERR_INVALID, "staged operands need a tensor-core precision");
+    std::vector<GemmArgs> gs = plan_contract(c.alpha, c.A, c.B, c.beta, c.C, c.so, c.sb, c.cache, c.cache_mask);
     if (tc && gs.size() == 1 && gs[0].M > 0 && gs[0].N > 0 && gs[0].batch > 0 && gs[0].K > 0 &&
-        tc_faster(ex, prec, gs[0])) {
+        (c.so || c.sb || tc_faster(ex, prec, gs[0]))) {
       grouped.push_back(gs[0]);
     } else {
-      for (const GemmArgs& g : gs) launch_gemm(ex, prec, g, nullptr);
+      for (const GemmArgs& g : gs) launch_gemm(ex, prec, g, tag);
     }
   }
-  if (!grouped.empty()) gemm_tc_group(ex, prec, grouped);
+  if (!grouped.empty()) gemm_tc_group(ex, prec, grouped, tag);
 }
 
 }  // namespace ccpnk

@@ -1434,12 +1434,16 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
 // prepared (operands staged), jobs of the same output mode share launches of up to GROUP_MAX
 // problems, then the split-k reductions run.
 template <bool BF>
-void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs) {
+void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs, const char* tag) {
   std::vector<std::unique_ptr<TcJob<BF>>> jobs;
+  double flops = 0.0;
   for (const auto& g : gs) {
     jobs.emplace_back(new TcJob<BF>());
     tc_prepare<BF>(ex, prec, g, *jobs.back());
+    flops += 2.0 * g.M * (double)g.N * g.K * g.batch;
   }
+  cudaEvent_t ev = nullptr;
+  if (ex.timing(tag)) ex.mark_begin(&ev);
   for (int epi = 0; epi < EPI_COUNT; ++epi) {
     std::vector<TcJob<BF>*> sel;
     for (auto& j : jobs)
@@ -1451,6 +1455,7 @@ void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>
     }
   }
   for (auto& j : jobs) tc_finish<BF>(ex, *j);
+  if (ev) ex.mark_end(tag, ev, flops);
 }
 
 // FP64-accurate contraction on the tensor cores (see oz_stage_kernel): stage both operands
@@ -1631,7 +1636,7 @@ void k_ladder_pm_stage(const Exec& ex, bool bf, int nseg, long long rows, int v,
   CC_CUDA(cudaGetLastError());
 }
 
-void gemm_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs) {
+void gemm_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs, const char* tag) {
   CC_REQUIRE(prec == CC_MIXED_TF32 || prec == CC_MIXED_TF32X3 || prec == CC_MIXED_BF16X3, CC_ERR_INVALID,
              "grouped launches run the single-precision tensor-core kinds");
   CC_REQUIRE(ex.dev_flag, CC_ERR_INVALID, "tensor-core contraction needs a device error flag");
@@ -1645,8 +1650,8 @@ void gemm_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs
     todo.push_back(g);
   }
   if (todo.empty()) return;
-  if (prec == CC_MIXED_BF16X3) run_tc_group<true>(ex, prec, todo);
-  else run_tc_group<false>(ex, prec, todo);
+  if (prec == CC_MIXED_BF16X3) run_tc_group<true>(ex, prec, todo, tag);
+  else run_tc_group<false>(ex, prec, todo, tag);
 }
 
 void gemm_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
