@@ -206,16 +206,51 @@ void Engine::ladder(const double* Xv, const double* Yv, int Paux, const double* 
   void* W2 = W2_.p;
   double* Tp = nullptr;
   double* Tmn = nullptr;
+  // FP64 (native or emulated) and double-float: when the split slabs of all blocks fit side by
+  // side in the same budget, every block's W+- goes into one array and the pair contractions
+  // run once over all blocks' rows (two contractions per ladder instead of two per block)
+  size_t all_rows = 0;
+  for (int a0 = 0; a0 < v; a0 += blk) all_rows += (size_t)std::min(blk, v - a0) * (v - a0);
+  const bool fused = !tensor && all_rows * (size_t)(Pv + Qv) * sizeof(double) <= kLadderGroupBytes;
   if (!tensor || pack) {
-    const size_t nbmax = (size_t)ladder_block_ * v;
-    if (!pmT_.p) {
-      pmT_.alloc(ex_.pool, (size_t)Po * Pv + (size_t)Qo * Qv + 1);
-      pmL_.alloc(ex_.pool, (size_t)(Po + Qo) * nbmax + 1);
-    }
-    if (!tensor && !pmW_.p) pmW_.alloc(ex_.pool, nbmax * (size_t)(Pv + Qv) + 1);
+    const size_t nbmax = fused ? all_rows : (size_t)ladder_block_ * v;
+    if (!pmT_.p) pmT_.alloc(ex_.pool, (size_t)Po * Pv + (size_t)Qo * Qv + 1);
+    if (pmL_.n < (size_t)(Po + Qo) * nbmax + 1) pmL_.alloc(ex_.pool, (size_t)(Po + Qo) * nbmax + 1);
+    if (!tensor && pmW_.n < nbmax * (size_t)(Pv + Qv) + 1) pmW_.alloc(ex_.pool, nbmax * (size_t)(Pv + Qv) + 1);
     Tp = pmT_.p;
     Tmn = Tp + (size_t)Po * Pv;
     k_ladder_pm_T(ex_, o, v, T, Tp, Tmn);
+  }
+  if (fused) {
+    const size_t ld = all_rows;
+    double* Wp = pmW_.p;
+    double* Wm = Wp + ld * Pv;
+    double* Lp = pmL_.p;
+    double* Lm = Lp + (size_t)Po * ld;
+    size_t r0 = 0;
+    for (int a0 = 0; a0 < v; a0 += blk) {
+      const int al = std::min(blk, v - a0), bl = v - a0;
+      TView Xa = view_strided(X + (size_t)a0 * v, "Pac", {Paux, al, v}, {(long long)v * v, v, 1});
+      TView Yb = view_strided(Y + (size_t)a0 * v, "Pbd", {Paux, bl, v}, {(long long)v * v, v, 1});
+      contract(ex_, prec, 1.0, Xa, Yb, 0.0, view(W_.p, "abcd", {al, bl, v, v}), tb);
+      k_ladder_pm_W(ex_, (size_t)al * bl, v, W_.p, Wp + r0 * Pv, Wm + r0 * Qv);
+      r0 += (size_t)al * bl;
+    }
+    const int nall = (int)ld;
+    contract(ex_, prec, 1.0, view(Tp, "xq", {Po, Pv}), view(Wp, "nq", {nall, Pv}), 0.0, view(Lp, "xn", {Po, nall}), tc);
+    if (Qo > 0 && Qv > 0)
+      contract(ex_, prec, 1.0, view(Tmn, "xq", {Qo, Qv}), view(Wm, "nq", {nall, Qv}), 0.0, view(Lm, "xn", {Qo, nall}),
+               tc);
+    else if (Qo > 0)
+      k_fill(ex_, (size_t)Qo * ld, 0.0, Lm);
+    r0 = 0;
+    for (int a0 = 0; a0 < v; a0 += blk) {
+      const int al = std::min(blk, v - a0), bl = v - a0;
+      k_ladder_pm_unpack(ex_, o, v, a0, al, bl, Lp + r0, Lm + r0, L, ld);
+      r0 += (size_t)al * bl;
+    }
+    k_ladder_mirror_add(ex_, o, v, blk, L, R);
+    return;
   }
   if (grouped) {
     std::vector<StagedOut> sos;

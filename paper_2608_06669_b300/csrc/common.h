@@ -336,7 +336,7 @@ void k_ladder_pm_stage(const Exec& ex, bool bf, int nseg, long long rows, int v,
                        long long kpP, void* Wm, long long kpQ);
 void k_ladder_pm_W(const Exec& ex, size_t rows, int v, const double* W, double* Wp, double* Wm);
 void k_ladder_pm_unpack(const Exec& ex, int o, int v, int a0, int al, int bl, const double* Lp, const double* Lm,
-                        double* L);
+                        double* L, size_t ld = 0);  // ld: row stride of L+ and L- (0: al bl)
 // L[p][q][r][s] = 2 g[p][q][r][s] - g[p][s][r][q] over an (o v o v) block
 void k_make_L_ovov(const Exec& ex, int o, int v, const double* g, double* L);
 // gamma[P] = sum_k A[P][k][k]

@@ -111,8 +111,9 @@ __global__ void ladder_pm_W_kernel(size_t rows, int v, const double* __restrict_
 }
 
 // L[i][j][a0 + a][a0 + b] = L+[(i<=j)][n] + L-[(i<j)][n] for i <= j and L+[(j<=i)][n] -
-// L-[(j<i)][n] for i > j, n = a bl + b (L+ symmetric and L- antisymmetric in i, j)
-__global__ void ladder_pm_unpack_kernel(int o, int v, int a0, int al, int bl, const double* __restrict__ Lp,
+// L-[(j<i)][n] for i > j, n = a bl + b (L+ symmetric and L- antisymmetric in i, j); the rows of
+// L+ and L- are ld apart
+__global__ void ladder_pm_unpack_kernel(int o, int v, int a0, int al, int bl, size_t ld, const double* __restrict__ Lp,
                                         const double* __restrict__ Lm, double* __restrict__ L) {
   const size_t nb = (size_t)al * bl, n = (size_t)o * o * nb;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -120,8 +121,8 @@ __global__ void ladder_pm_unpack_kernel(int o, int v, int a0, int al, int bl, co
     const int j = (int)(ij % o), i = (int)(ij / o);
     const int a = (int)(nn / bl), b = (int)(nn % bl);
     double val;
-    if (i <= j) val = Lp[pair_le(i, j, o) * nb + nn] + (i < j ? Lm[pair_lt(i, j, o) * nb + nn] : 0.0);
-    else val = Lp[pair_le(j, i, o) * nb + nn] - Lm[pair_lt(j, i, o) * nb + nn];
+    if (i <= j) val = Lp[pair_le(i, j, o) * ld + nn] + (i < j ? Lm[pair_lt(i, j, o) * ld + nn] : 0.0);
+    else val = Lp[pair_le(j, i, o) * ld + nn] - Lm[pair_lt(j, i, o) * ld + nn];
     L[(((size_t)i * o + j) * v + a0 + a) * v + a0 + b] = val;
   }
 }
@@ -415,10 +416,11 @@ void k_ladder_pm_W(const Exec& ex, size_t rows, int v, const double* W, double* 
   LAUNCH_CHECK();
 }
 void k_ladder_pm_unpack(const Exec& ex, int o, int v, int a0, int al, int bl, const double* Lp, const double* Lm,
-                        double* L) {
+                        double* L, size_t ld) {
   const size_t n = (size_t)o * o * al * bl;
   if (!n) return;
-  ladder_pm_unpack_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, a0, al, bl, Lp, Lm, L);
+  ladder_pm_unpack_kernel<<<grid_for(ex, n), TPB, 0, ex.stream>>>(o, v, a0, al, bl, ld ? ld : (size_t)al * bl, Lp, Lm,
+                                                                   L);
   LAUNCH_CHECK();
 }
 void k_make_u(const Exec& ex, int o, int v, const double* t, double* u) {
