@@ -35,6 +35,13 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # TF32 dense tensor peak: measured bf16 burst x the nominal TF32/BF16 ratio (1.1 / 2.25)
 TF32_RATIO = 1.1 / 2.25
 OZ_PRODUCTS = 45  # BF16 slice products per FP64-equivalent product of the emulation (9 slices)
+# DRAM read + write bytes per launch of a tagged GEMM, from one ncu capture of the current build:
+# (bytes, where they come from)
+TRAFFIC_FROM_CAPTURE = {
+    "emu": (58.4e6, "ncu launch list of one o10v90 emulated residual (profiles/oz_gemm_emu_ladder_build_o10v90.md): "
+                    "mean over the ladder-build blocks summed on chip of their two digit-staging launches and the "
+                    "oz_gemm_kernel launch; a constant from that capture, not measured by this run"),
+}
 
 
 def rank_info():
@@ -519,7 +526,12 @@ def run_ours(args):
     dom = max(roofs, key=lambda k: tags[k][1]) if roofs else None
     roof = dict(roofs[dom]) if dom else None
     if roof:
-        roof["traffic"] = None  # DRAM bytes of this kernel come from the ncu summaries in profiles/
+        # DRAM bytes per launch from one ncu capture of the same kernels (a constant, labelled as
+        # such; null for a kernel without a capture of the current build)
+        cap = TRAFFIC_FROM_CAPTURE.get(dom)
+        roof["traffic"] = cap[0] if cap else None
+        if cap:
+            roof["traffic_source"] = cap[1]
         roof["share_of_profiled_solves"] = tags[dom][1] / 1e3 / t_prof
         roof["measured_on"] = "repeats of the timed solve with the kernel timer on (eager JVPs), right after it"
     cpu = None
