@@ -104,35 +104,54 @@ constexpr int ROW_PIECE = 256;
 // operand, three segments [hi|hi|lo] and [hi|lo|hi] on the two operands give the three-pass
 // split product hi hi + hi lo + lo hi along one long k. One warp per piece of a staged row:
 // the row's source offset is located once, and the lanes walk k.
+// Several operands staged by one launch: their descriptors and the prefix sums of their work
+// items (batch x rows_pad x row pieces each) are a grid-constant parameter, and every warp walks
+// the combined item list, finding its operand by the prefix sums.
+struct GatherDesc {
+  const double* src;
+  void* out;
+  CIdx rix, kix, bix;
+  int rows, K, batch, rows_pad, k_pad, nseg, seg_lo;
+};
+constexpr int GATHER_MAX = 24;
+struct GatherList {
+  GatherDesc d[GATHER_MAX];
+  long long item0[GATHER_MAX + 1];
+  int n;
+};
+
 template <typename T>
-__global__ void gather_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
-                              int batch, int rows_pad, int k_pad, int nseg, int seg_lo, T* __restrict__ out) {
+__global__ void gather_kernel(const __grid_constant__ GatherList L) {
   const int lane = threadIdx.x & 31;
-  const int pieces = (k_pad + ROW_PIECE - 1) / ROW_PIECE;
-  const long long items = (long long)batch * rows_pad * pieces;
-  const size_t row_len = (size_t)nseg * k_pad;
+  const long long total = L.item0[L.n];
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long it = w0; it < items; it += nw) {
-    const long long q = it / pieces;  // staged row b * rows_pad + r
-    const int k0 = (int)(it - q * pieces) * ROW_PIECE, k1 = min(k_pad, k0 + ROW_PIECE);
-    const int b = (int)(q / rows_pad), r = (int)(q - (long long)b * rows_pad);
-    T* row = out + (size_t)q * row_len;
-    if (r >= rows) {
+  int gi = 0;
+  for (long long it = w0; it < total; it += nw) {
+    while (it >= L.item0[gi + 1]) ++gi;  // a warp's items only grow
+    const GatherDesc& d = L.d[gi];
+    const int pieces = (d.k_pad + ROW_PIECE - 1) / ROW_PIECE;
+    const size_t row_len = (size_t)d.nseg * d.k_pad;
+    const long long li = it - L.item0[gi];
+    const long long q = li / pieces;  // staged row b * rows_pad + r
+    const int k0 = (int)(li - q * pieces) * ROW_PIECE, k1 = min(d.k_pad, k0 + ROW_PIECE);
+    const int b = (int)(q / d.rows_pad), r = (int)(q - (long long)b * d.rows_pad);
+    T* row = static_cast<T*>(d.out) + (size_t)q * row_len;
+    if (r >= d.rows) {
       T z, zl;
       split(0.0f, z, zl);
       for (int k = k0 + lane; k < k1; k += 32)
-        for (int s = 0; s < nseg; ++s) row[(size_t)s * k_pad + k] = z;
+        for (int s = 0; s < d.nseg; ++s) row[(size_t)s * d.k_pad + k] = z;
       continue;
     }
-    const double* srow = src + cidx(bix, b) + cidx(rix, r);
+    const double* srow = d.src + cidx(d.bix, b) + cidx(d.rix, r);
     CWalk kw;
-    kw.init(kix, k0 + lane);
+    kw.init(d.kix, k0 + lane);
     for (int k = k0 + lane; k < k1; k += 32) {
       T hi, lo;
-      split(k < K ? (float)srow[kw.off] : 0.0f, hi, lo);
-      for (int s = 0; s < nseg; ++s) row[(size_t)s * k_pad + k] = ((seg_lo >> s) & 1) ? lo : hi;
-      kw.step(kix, 32);
+      split(k < d.K ? (float)srow[kw.off] : 0.0f, hi, lo);
+      for (int s = 0; s < d.nseg; ++s) row[(size_t)s * d.k_pad + k] = ((d.seg_lo >> s) & 1) ? lo : hi;
+      kw.step(d.kix, 32);
     }
   }
 }
@@ -1225,8 +1244,35 @@ struct TcJob {
   DBuf<double> stA, stB, part;
 };
 
+// Operands waiting to be staged: collected while contractions are prepared, then staged by as
+// few launches as possible (GATHER_MAX operands each) before the GEMMs that read them.
+template <typename T>
+struct GatherBatch {
+  std::vector<GatherDesc> pend;
+  void flush(const Exec& ex) {
+    for (size_t i = 0; i < pend.size(); i += GATHER_MAX) {
+      GatherList L;
+      memset(&L, 0, sizeof(L));
+      L.n = (int)std::min<size_t>(GATHER_MAX, pend.size() - i);
+      L.item0[0] = 0;
+      for (int j = 0; j < L.n; ++j) {
+        const GatherDesc& d = pend[i + j];
+        L.d[j] = d;
+        L.item0[j + 1] = L.item0[j] + (long long)d.batch * d.rows_pad * ((d.k_pad + ROW_PIECE - 1) / ROW_PIECE);
+      }
+      const long long items = L.item0[L.n];
+      const int blocks = (int)std::max<long long>(1, std::min<long long>((items + 7) / 8, (long long)ex.sm_count * 16));
+      gather_kernel<T><<<blocks, 256, 0, ex.stream>>>(L);
+      ex.count();
+    }
+    pend.clear();
+    CC_CUDA(cudaGetLastError());
+  }
+};
+
 template <bool BF>
-void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>& job) {
+void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>& job,
+                GatherBatch<typename Elt<BF>::T>& gb) {
   using T = typename Elt<BF>::T;
   constexpr int TK = Elt<BF>::TK;
   job.g = g;
@@ -1235,14 +1281,9 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
   // the split precisions stage [hi|hi|lo] against [hi|lo|hi] along a three times longer k
   const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
   const int kk = nseg * k_pad;
-  // warp-per-row-piece kernels: eight pieces per 256-thread block and pass
-  auto blocks_for_rows = [&](size_t rows, size_t row_len) {
-    const size_t items = rows * ((row_len + ROW_PIECE - 1) / ROW_PIECE);
-    return (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
-  };
   // Staged copy of one operand: taken from the cache when the caller marked the operand as
   // fixed and it was staged before with the same layout, else gathered (into the cache when
-  // it is marked and fits, into a temporary otherwise).
+  // it is marked and fits, into a temporary otherwise) by the batch's next launch.
   auto stage = [&](int which, const double* src, const CIdx& rix, const CIdx& kix, const CIdx& bix, int rows,
                    int rows_pad, int seg_lo, DBuf<double>& tmp) -> T* {
     const size_t dbl = ((size_t)g.batch * rows_pad * kk * sizeof(T) + 7) / 8;
@@ -1271,9 +1312,20 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
       tmp.alloc(ex.pool, dbl);
       dst = tmp.p;
     }
-    gather_kernel<T><<<blocks_for_rows((size_t)g.batch * rows_pad, k_pad), 256, 0, ex.stream>>>(
-        src, rix, kix, bix, rows, g.K, g.batch, rows_pad, k_pad, nseg, seg_lo, reinterpret_cast<T*>(dst));
-    ex.count();
+    GatherDesc d;
+    d.src = src;
+    d.out = dst;
+    d.rix = rix;
+    d.kix = kix;
+    d.bix = bix;
+    d.rows = rows;
+    d.K = g.K;
+    d.batch = g.batch;
+    d.rows_pad = rows_pad;
+    d.k_pad = k_pad;
+    d.nseg = nseg;
+    d.seg_lo = seg_lo;
+    gb.pend.push_back(d);
     return reinterpret_cast<T*>(dst);
   };
   T* fA = stage(1, g.A, g.am, g.ak, g.ab, g.M, rowsA, nseg == 3 ? 0b100 : 0, job.stA);
@@ -1288,7 +1340,6 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
   } else {
     fB = stage(2, g.B, g.bn, g.bk, g.bb, g.N, rowsB, nseg == 3 ? 0b010 : 0, job.stB);
   }
-  CC_CUDA(cudaGetLastError());
   CC_REQUIRE(!g.so || g.beta == 0.0, CC_ERR_INVALID, "a staged output cannot accumulate");
   job.mA = make_map(fA, kk, rowsA, g.batch, TM, BF);
   job.mB = make_map(fB, kk, rowsBmap, g.batch, TN, BF);
@@ -1421,7 +1472,9 @@ void tc_finish(const Exec& ex, TcJob<BF>& job) {
 template <bool BF>
 void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* tag) {
   TcJob<BF> job;
-  tc_prepare<BF>(ex, prec, g, job);
+  GatherBatch<typename Elt<BF>::T> gb;
+  tc_prepare<BF>(ex, prec, g, job, gb);
+  gb.flush(ex);
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
   TcJob<BF>* one = &job;
@@ -1436,12 +1489,14 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
 template <bool BF>
 void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>& gs, const char* tag) {
   std::vector<std::unique_ptr<TcJob<BF>>> jobs;
+  GatherBatch<typename Elt<BF>::T> gb;
   double flops = 0.0;
   for (const auto& g : gs) {
     jobs.emplace_back(new TcJob<BF>());
-    tc_prepare<BF>(ex, prec, g, *jobs.back());
+    tc_prepare<BF>(ex, prec, g, *jobs.back(), gb);
     flops += 2.0 * g.M * (double)g.N * g.K * g.batch;
   }
+  gb.flush(ex);
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
   for (int epi = 0; epi < EPI_COUNT; ++epi) {
