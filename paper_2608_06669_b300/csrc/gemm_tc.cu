@@ -447,7 +447,9 @@ __device__ __forceinline__ int oz_level_shift(int L) {
   return L <= OZ_LH ? OZ_BETA * (OZ_LH - L) : OZ_BETA * (OZ_S + 1 - L);
 }
 // acc_h 2^OZ_HSH + acc_l as a double: the exact sum is hi 2^OZ_HSH + lo with 0 <= lo < 2^OZ_HSH;
-// hi is exact in FP64 (|hi| < 2^53 for k_pad < 2^22), so the one rounding is the fma's.
+// hi is exact in FP64 for k_pad < 2^22 (|hi| < 2^53), so the one rounding is the fma's (beyond
+// that, up to the 2^24 the callers allow, hi is rounded first: within an ulp, no longer one
+// rounding).
 __device__ __forceinline__ double oz_fixed_value(long long acc_h, long long acc_l) {
   const long long hi = acc_h + (acc_l >> OZ_HSH);
   const long long lo = acc_l & ((1ll << OZ_HSH) - 1);
@@ -1513,10 +1515,10 @@ void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>
   if (ev) ex.mark_end(tag, ev, flops);
 }
 
-// FP64-accurate contraction on the tensor cores (see oz_stage_kernel): stage both operands
-// as OZ_S BF16 digit slices with per-row exponents, run every (level, chunk) slice product as a
-// split of one persistent kind::f16 launch writing exact FP32 partial sums, and combine them in
-// integer fixed point into C = alpha A B + beta C.
+// FP64-accurate contraction on the tensor cores (Ozaki splitting, above): stage both operands
+// as OZ_S BF16 digit slices with per-row exponents, run every (level, chunk) slice product on
+// kind::f16 (on chip, or as splits writing exact FP32 partial sums that a combine pass adds),
+// and add the levels in integer fixed point into C = alpha A B + beta C.
 int oz_splits(int kseg, int nk) {
   int n = 0;
   for (int L = 2; L <= OZ_S + 1; ++L) n += ((L - 1) * kseg + nk - 1) / nk;
@@ -1543,7 +1545,7 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   constexpr int TK = Elt<true>::TK;
   const int k_pad = (g.K + TK - 1) / TK * TK;
   const int kseg = k_pad / TK, kk = OZ_S * k_pad;
-  const int nk = std::max(1, std::min(64, ex.emu_chunk));
+  const int nk = std::max(1, std::min(OZ_NK, ex.emu_chunk));
   const int nsplit = oz_splits(kseg, nk);
   CC_REQUIRE(k_pad < (1 << 24), CC_ERR_INVALID, "FP64-emulated contraction: sum longer than 2^24");
   const bool onchip = oz_onchip(ex, g, kseg);
