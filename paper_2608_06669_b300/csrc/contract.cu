@@ -349,6 +349,34 @@ __global__ void gemv_f64_kernel(GemmArgs g, int trans) {
 // C = alpha * sum_s part[s] + beta * C, the splits added in order. One warp per piece of
 // 256 elements of an output row: the row offset is located once and the column digits are
 // carried, not divided out per element.
+// the same with few outputs and many splits: 32 consecutive outputs per block of eight warps,
+// warp w adding the splits w, w + 8, ... in order, warp 0 adding the eight sums in order
+__global__ void __launch_bounds__(256) splitk_reduce_small_kernel(GemmArgs g) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t tot = (size_t)g.M * g.N * g.batch;
+  for (size_t o0 = (size_t)blockIdx.x * 32; o0 < tot; o0 += (size_t)gridDim.x * 32) {
+    const size_t o = o0 + lane;
+    double s = 0.0;
+    if (o < tot)
+      for (int p = w; p < g.splits; p += 8) s += g.part[(size_t)p * tot + o];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && o < tot) {
+      double t = red[0][lane];
+#pragma unroll
+      for (int j = 1; j < 8; ++j) t += red[j][lane];
+      const size_t q = o / g.N;  // output row b * M + m
+      const int n = (int)(o - q * g.N);
+      const int b = (int)(q / g.M), m = (int)(q - (size_t)b * g.M);
+      double* c = g.C + cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
+      const double val = g.alpha * t;
+      *c = g.beta == 0.0 ? val : fma(g.beta, *c, val);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void splitk_reduce_kernel(GemmArgs g) {
   const int lane = threadIdx.x & 31;
   const size_t tot = (size_t)g.M * g.N * g.batch;
@@ -579,7 +607,13 @@ void launch_gemm(const Exec& ex, cc_precision prec, GemmArgs g, const char* tag)
   if (splits > 1) {
     const size_t items = (size_t)g.batch * g.M * ((g.N + 255) / 256);
     int blocks = (int)std::max<size_t>(1, std::min<size_t>((items + 7) / 8, (size_t)ex.sm_count * 16));
-    splitk_reduce_kernel<<<blocks, 256, 0, ex.stream>>>(g);
+    const size_t outs = (size_t)g.batch * g.M * g.N;
+    if (outs < 65536 && splits >= 16) {  // few outputs, many splits: spread the splits
+      const int sblocks = (int)std::max<size_t>(1, std::min<size_t>((outs + 31) / 32, (size_t)ex.sm_count * 16));
+      splitk_reduce_small_kernel<<<sblocks, 256, 0, ex.stream>>>(g);
+    } else {
+      splitk_reduce_kernel<<<blocks, 256, 0, ex.stream>>>(g);
+    }
     ex.count();
     CC_CUDA(cudaGetLastError());
   }

@@ -249,6 +249,45 @@ __global__ void __launch_bounds__(256) ladder_pm_stage_kernel(long long rows, in
   }
 }
 
+// split-k for few outputs and many splits: a block of eight warps takes 32 consecutive outputs
+// (lanes along the outputs, so the reads coalesce), warp w adds the splits w, w + 8, ... in
+// order, and warp 0 adds the eight warp sums in order: a fixed summation order for a given
+// split count, with the splits instead of the outputs spread over the warps.
+template <typename T>
+__global__ void __launch_bounds__(256) tc_splitk_reduce_small_kernel(GemmArgs g, const float* __restrict__ part,
+                                                                     int splits, T* Cs, long long kpad, int nseg,
+                                                                     int seglo) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t tot = (size_t)g.batch * g.M * g.N;
+  for (size_t o0 = (size_t)blockIdx.x * 32; o0 < tot; o0 += (size_t)gridDim.x * 32) {
+    const size_t o = o0 + lane;
+    double s = 0.0;
+    if (o < tot)
+      for (int p = w; p < splits; p += 8) s += (double)part[(size_t)p * tot + o];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && o < tot) {
+      double t = red[0][lane];
+#pragma unroll
+      for (int j = 1; j < 8; ++j) t += red[j][lane];
+      const size_t q = o / g.N;  // output row b * M + m
+      const int n = (int)(o - q * g.N);
+      const int b = (int)(q / g.M), m = (int)(q - (size_t)b * g.M);
+      const long long off = cidx(g.cb, b) + cidx(g.cm, m) + cidx(g.cn, n);
+      if (Cs && nseg == 0) {
+        reinterpret_cast<float*>(Cs)[off] = (float)(g.alpha * t);
+      } else if (Cs) {
+        store_staged(Cs + off, kpad, nseg, seglo, (float)(g.alpha * t));
+      } else {
+        double* c = g.C + off;
+        *c = g.beta == 0.0 ? g.alpha * t : fma(g.beta, *c, g.alpha * t);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void scale_c_kernel(GemmArgs g) {  // K == 0: C = beta C
   const size_t tot = (size_t)g.batch * g.M * g.N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
@@ -1460,6 +1499,15 @@ void tc_finish(const Exec& ex, TcJob<BF>& job) {
   using T = typename Elt<BF>::T;
   const GemmArgs& g = job.g;
   if (job.a.splits <= 1) return;
+  const size_t outs = (size_t)g.batch * g.M * g.N;
+  if (outs < 65536 && job.a.splits >= 16) {  // few outputs, many splits: spread the splits
+    const int rblocks = (int)std::max<size_t>(1, std::min<size_t>((outs + 31) / 32, (size_t)ex.sm_count * 16));
+    tc_splitk_reduce_small_kernel<T><<<rblocks, 256, 0, ex.stream>>>(
+        g, job.a.part, job.a.splits, static_cast<T*>(job.a.Cs), job.a.cs_kpad, job.a.cs_nseg, job.a.cs_seglo);
+    ex.count();
+    CC_CUDA(cudaGetLastError());
+    return;
+  }
   // short outputs are cut into warp-sized pieces so that enough warps share the reads
   const size_t rows = (size_t)g.batch * g.M;
   const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
