@@ -55,7 +55,10 @@ typedef enum {
   CC_MIXED_BF16X3 = 2,  /* 3-pass BF16 split: x = hi + lo in BF16, a b ~ hi hi + hi lo + lo hi on
                            tcgen05 kind::f16, FP32 accumulate (about 16 significant bits) */
   CC_MIXED_TF32X3 = 3,  /* 3-pass TF32 split: x = hi + lo, a b ~ hi hi + hi lo + lo hi on tcgen05,
-                           FP32 accumulate (about FP32 accuracy at a third of the TF32 rate) */
+                           FP32 accumulate (about FP32 accuracy at a third of the TF32 rate).
+                           In the three single-precision tensor-core kinds, contractions too thin
+                           for the tensor cores' tiles run on the FP32 pipe (FP32 products, at
+                           most 512 terms per FP32 sum, FP64 split-k and output) */
   CC_DF64 = 4,          /* double-float: FP64 operands as FP32 pairs on the FP32 pipe (error-free
                            products, two-sum accumulation; about 48 significant bits), for the
                            residual when FP64 FMA throughput is the limit */
