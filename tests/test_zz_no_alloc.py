@@ -3,15 +3,17 @@
 For callers that cannot call cudaMalloc at the point where they need the energy (another
 framework's arena, a real-time loop, memory reserved up front). The entry point is called
 through the C ABI with device buffers the test owns, twice in a row on different amplitudes,
-and each result must equal the energy cc_residual returns for the same amplitudes, to the
-FP64 parity tolerance. This file sorts last so that a run stopping at its first failure has
-already run every other test; it also passes on its own in a fresh process.
+and each result must equal the oracle's energy and the energy cc_residual returns for the
+same amplitudes, to the FP64 parity tolerance. This file sorts last so that a run stopping at
+its first failure has already run every other test; it also passes on its own in a fresh
+process.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import dfccsd as cc
 from paper_2608_06669_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +43,8 @@ def test_energy_without_allocation_matches_cc_residual(cuda_device):
         torch.cuda.synchronize()
         e = float(out.item())
         assert abs(e - e_ref) <= 1e-10 * max(1.0, abs(e_ref)), (call, e, e_ref)
+        e_or = cc.energy(s.fock, s.B, s.o, t1, t2)
+        assert abs(e - e_or) <= 1e-10 * max(1.0, abs(e_or)), (call, e, e_or)
     # NULL arguments are rejected before any launch
     assert L.cc_energy_noalloc(g.h, None, None, None, None) == -1
     g.close()
