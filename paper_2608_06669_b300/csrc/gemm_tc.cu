@@ -900,10 +900,18 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
               if (ro >= 0 && n_ok) cc[ro] = g.alpha * (double)tile[rr * 33 + lane];
             }
           } else {
-#pragma unroll 8
+            // the 32 rows' old values are read first, so that all their loads are in flight at
+            // once (an accumulating epilogue otherwise waits for one load latency per few rows)
+            double old[32];
+#pragma unroll
             for (int rr = 0; rr < 32; ++rr) {
               const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
-              if (ro >= 0 && n_ok) cc[ro] = fma(g.beta, cc[ro], g.alpha * (double)tile[rr * 33 + lane]);
+              old[rr] = (ro >= 0 && n_ok) ? cc[ro] : 0.0;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) {
+              const long long ro = __shfl_sync(0xffffffffu, my_off, rr);
+              if (ro >= 0 && n_ok) cc[ro] = fma(g.beta, old[rr], g.alpha * (double)tile[rr * 33 + lane]);
             }
           }
         }
