@@ -621,10 +621,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D = F32, A = B = TF32 or BF16, both K-major, N = TN, M = TM
-template <bool BF>
+// instruction descriptor: D = F32, A = B = TF32 or BF16, both K-major, N = TNT, M = TM
+template <bool BF, int TNT>
 constexpr uint32_t idesc() {
-  return (1u << 4) | (Elt<BF>::FMT << 7) | (Elt<BF>::FMT << 10) | ((uint32_t)(TN >> 3) << 17) |
+  return (1u << 4) | (Elt<BF>::FMT << 7) | (Elt<BF>::FMT << 10) | ((uint32_t)(TNT >> 3) << 17) |
          ((uint32_t)(TM >> 4) << 24);
 }
 
@@ -650,6 +650,7 @@ __host__ __device__ __forceinline__ int oz_split_range(int S, int kseg, int nk, 
 }
 
 // tile t -> (split, batch entry, first row, first column, k blocks of A and of B, their count)
+template <int TNT>
 __device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int& bz, int& m0, int& n0, int& kA0,
                                             int& kB0, int& nkb) {
   const int per = g.num_m * g.num_n;
@@ -659,10 +660,10 @@ __device__ __forceinline__ void tile_coords(const TcArgs& g, int t, int& sp, int
   const int r = t - outer * per;
   if (g.m_fast) {
     m0 = (r % g.num_m) * TM;
-    n0 = (r / g.num_m) * TN;
+    n0 = (r / g.num_m) * TNT;
   } else {
     m0 = (r / g.num_n) * TM;
-    n0 = (r % g.num_n) * TN;
+    n0 = (r % g.num_n) * TNT;
   }
   if (g.oz_S > 0) {
     oz_split_range(g.oz_S, g.oz_kseg, g.oz_nk, sp, kA0, kB0, nkb);
@@ -712,8 +713,11 @@ constexpr size_t SMEM_BYTES = 1024 + SMEM_USED;
 //   warps 2-9: epilogue (TMEM lane quadrant = warp % 4, two warps per quadrant on the two
 //              column halves), releasing an accumulator as soon as it has been read, so the
 //              next tile's MMAs overlap this tile's stores
-template <bool BF, int EPI, int MAXP>
+// Tiles are TM x TNT, TNT = 256 or 128 (the narrower tile for outputs with fewer tiles than SMs:
+// twice the tiles for the same output); the shared-memory ring keeps its 256-row B stages.
+template <bool BF, int EPI, int MAXP, int TNT>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ TcGroup<MAXP> G) {
+  static_assert(TNT == 256 || TNT == 128, "tile width");
   constexpr int TK = Elt<BF>::TK, UK = Elt<BF>::UK;
   using T = typename Elt<BF>::T;
   extern __shared__ uint8_t smem_raw[];
@@ -740,7 +744,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(2 * TNT)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -760,12 +764,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         p = group_problem(G, t, p);
         const TcArgs& g = G.args[p];
         int sp, bz, m0, n0, kA0, kB0, nkb;
-        tile_coords(g, t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
+        tile_coords<TNT>(g, t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
         for (int kb = 0; kb < nkb; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
           if (!mbar_wait(empty0 + 8 * s, ph ^ 1, wait_ns)) { ok = false; break; }
-          mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
+          mbar_expect_tx(full0 + 8 * s, A_BYTES + TNT * 128);
           tma_load_3d(smem_u32(sA + s * A_BYTES), &G.tmA[p], full0 + 8 * s, (kA0 + kb) * TK, m0, bz);
           tma_load_3d(smem_u32(sB + s * B_BYTES), &G.tmB[p], full0 + 8 * s, (kB0 + kb) * TK, n0, bz);
         }
@@ -785,10 +789,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         const uint32_t use = (uint32_t)(it >> 1);
         if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, wait_ns)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(acc * TN);
+        const uint32_t d = tmem + (uint32_t)(acc * TNT);
         p = group_problem(G, t, p);
         int sp, bz, m0, n0, kA0, kB0, nkb;
-        tile_coords(G.args[p], t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
+        tile_coords<TNT>(G.args[p], t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
         for (int kb = 0; kb < nkb; ++kb, ++q) {
           const int s = q % STAGES;
           const uint32_t ph = (q / STAGES) & 1;
@@ -804,12 +808,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             if constexpr (BF) {
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                  "l"(da), "l"(db), "r"(idesc<BF>()), "r"(accum)
+                  "l"(da), "l"(db), "r"(idesc<BF, TNT>()), "r"(accum)
                   : "memory");
             } else {
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                  "l"(da), "l"(db), "r"(idesc<BF>()), "r"(accum)
+                  "l"(da), "l"(db), "r"(idesc<BF, TNT>()), "r"(accum)
                   : "memory");
             }
           }
@@ -840,7 +844,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       const TcArgs& g = G.args[p];
       const float alpha_f = (float)g.alpha;
       int sp, bz, m0, n0, kA0, kB0, nkb;
-      tile_coords(g, t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
+      tile_coords<TNT>(g, t - G.tile0[p], sp, bz, m0, n0, kA0, kB0, nkb);
       // each lane locates one of the warp's 32 rows once; the store loop broadcasts them
       const int my_row = m0 + quad * 32 + lane;
       long long my_off = -1;
@@ -848,12 +852,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         my_off = EPI == EPI_PART ? (((long long)sp * g.batch + bz) * g.M + my_row) * (long long)g.N
                                  : cidx(g.cb, bz) + cidx(g.cm, my_row);
 #pragma unroll 1
-      for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 32) {
+      for (int c0 = half * (TNT / 2); c0 < (half + 1) * (TNT / 2); c0 += 32) {
         // the rest of the tile lies past the last column, or this warp's 32 rows past the last
         // row (both warp-uniform)
         if (n0 + c0 >= g.N || m0 + quad * 32 >= g.M) break;
         uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TN + c0);
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TNT + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%"
             "22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -927,7 +931,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TNT) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -1290,6 +1294,7 @@ struct TcJob {
   CUtensorMap mA, mB;
   TcArgs a{};
   int epi = EPI_F64;
+  int tn = TN;  // tile width: TN, or 128 when the output has fewer TN-wide tiles than SMs
   DBuf<double> stA, stB, part;
 };
 
@@ -1325,7 +1330,12 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
   using T = typename Elt<BF>::T;
   constexpr int TK = Elt<BF>::TK;
   job.g = g;
-  const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + TN - 1) / TN * TN;
+  // outputs with fewer TN-wide tiles than SMs take 128-wide tiles: twice the tiles (and CTAs
+  // writing the output) before any split of k
+  const long long tiles_wide = (long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN) * g.batch;
+  const int tn = tiles_wide < ex.sm_count ? 128 : TN;
+  job.tn = tn;
+  const int rowsA = (g.M + TM - 1) / TM * TM, rowsB = (g.N + tn - 1) / tn * tn;
   const int k_pad = (g.K + TK - 1) / TK * TK;
   // the split precisions stage [hi|hi|lo] against [hi|lo|hi] along a three times longer k
   const int nseg = prec == CC_MIXED_TF32 ? 1 : 3;
@@ -1382,7 +1392,7 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
   int rowsBmap = rowsB;
   if (g.sb) {
     // B was written in staging layout by an earlier contraction
-    CC_REQUIRE(g.batch == 1 && g.sb->kk == kk && g.sb->rows_pad >= rowsB && g.sb->rows_pad % TN == 0,
+    CC_REQUIRE(g.batch == 1 && g.sb->kk == kk && g.sb->rows_pad >= rowsB && g.sb->rows_pad % tn == 0,
                CC_ERR_INVALID, "staged operand does not match the contraction");
     fB = static_cast<T*>(const_cast<void*>(g.sb->base));
     rowsBmap = g.sb->rows_pad;
@@ -1391,13 +1401,13 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
   }
   CC_REQUIRE(!g.so || g.beta == 0.0, CC_ERR_INVALID, "a staged output cannot accumulate");
   job.mA = make_map(fA, kk, rowsA, g.batch, TM, BF);
-  job.mB = make_map(fB, kk, rowsBmap, g.batch, TN, BF);
+  job.mB = make_map(fB, kk, rowsBmap, g.batch, tn, BF);
   TcArgs& a = job.a;
   a.M = g.M;
   a.N = g.N;
   a.kblocks = kk / TK;
   a.num_m = rowsA / TM;
-  a.num_n = rowsB / TN;
+  a.num_n = rowsB / tn;
   a.batch = g.batch;
   // Tiles that run at the same time share operand tiles through L2: the shorter of the two
   // tile dimensions runs fastest, so a wave of CTAs covers whole columns (or rows) of tiles
@@ -1412,7 +1422,7 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
   int splits = 1;
   if (base_tiles < ex.sm_count && a.kblocks >= 8) {
     const double sm_rate = (BF ? 2.0 : 1.0) * 5.8e12;  // dense MMA flop/s of one SM
-    const double t_tile = 2.0 * TM * TN * (double)a.kblocks * TK / sm_rate;
+    const double t_tile = 2.0 * TM * tn * (double)a.kblocks * TK / sm_rate;
     const double t_fix = 3e-6, hbm = 6.0e12;
     const double part_bytes = 8.0 * (double)g.batch * g.M * g.N;  // FP32 written + read, per split
     auto model = [&](int sp) {
@@ -1467,10 +1477,10 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
 
 // One launch over n jobs of one output mode (n <= MAXP): their tiles numbered consecutively,
 // one persistent CTA per SM at most.
-template <bool BF, int EPI, int MAXP>
+template <bool BF, int EPI, int MAXP, int TNT>
 void tc_launch_group(const Exec& ex, TcJob<BF>* const* jobs, int n) {
   static std::atomic<uint64_t> attr_done{0};
-  auto kern = gemm_tc_kernel<BF, EPI, MAXP>;
+  auto kern = gemm_tc_kernel<BF, EPI, MAXP, TNT>;
   ensure_smem_attr(kern, attr_done);
   TcGroup<MAXP> G;
   memset(&G, 0, sizeof(G));
@@ -1490,15 +1500,20 @@ void tc_launch_group(const Exec& ex, TcJob<BF>* const* jobs, int n) {
   CC_CUDA(cudaGetLastError());
 }
 
-template <bool BF, int MAXP>
-void tc_launch(const Exec& ex, int epi, TcJob<BF>* const* jobs, int n) {
+template <bool BF, int MAXP, int TNT>
+void tc_launch_tn(const Exec& ex, int epi, TcJob<BF>* const* jobs, int n) {
   switch (epi) {
-    case EPI_PART: tc_launch_group<BF, EPI_PART, MAXP>(ex, jobs, n); break;
-    case EPI_STAGED1: tc_launch_group<BF, EPI_STAGED1, MAXP>(ex, jobs, n); break;
-    case EPI_STAGED3: tc_launch_group<BF, EPI_STAGED3, MAXP>(ex, jobs, n); break;
-    case EPI_F32: tc_launch_group<BF, EPI_F32, MAXP>(ex, jobs, n); break;
-    default: tc_launch_group<BF, EPI_F64, MAXP>(ex, jobs, n); break;
+    case EPI_PART: tc_launch_group<BF, EPI_PART, MAXP, TNT>(ex, jobs, n); break;
+    case EPI_STAGED1: tc_launch_group<BF, EPI_STAGED1, MAXP, TNT>(ex, jobs, n); break;
+    case EPI_STAGED3: tc_launch_group<BF, EPI_STAGED3, MAXP, TNT>(ex, jobs, n); break;
+    case EPI_F32: tc_launch_group<BF, EPI_F32, MAXP, TNT>(ex, jobs, n); break;
+    default: tc_launch_group<BF, EPI_F64, MAXP, TNT>(ex, jobs, n); break;
   }
+}
+template <bool BF, int MAXP>
+void tc_launch(const Exec& ex, int epi, int tn, TcJob<BF>* const* jobs, int n) {
+  if (tn == 128) tc_launch_tn<BF, MAXP, 128>(ex, epi, jobs, n);
+  else tc_launch_tn<BF, MAXP, TN>(ex, epi, jobs, n);
 }
 
 // split-k: the partial sums of a finished job added in a fixed order into C (or its staging)
@@ -1536,7 +1551,7 @@ void run_tc(const Exec& ex, cc_precision prec, const GemmArgs& g, const char* ta
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
   TcJob<BF>* one = &job;
-  tc_launch<BF, 1>(ex, job.epi, &one, 1);
+  tc_launch<BF, 1>(ex, job.epi, job.tn, &one, 1);
   tc_finish<BF>(ex, job);
   if (ev) ex.mark_end(tag, ev, 2.0 * g.M * (double)g.N * g.K * g.batch);
 }
@@ -1557,16 +1572,17 @@ void run_tc_group(const Exec& ex, cc_precision prec, const std::vector<GemmArgs>
   gb.flush(ex);
   cudaEvent_t ev = nullptr;
   if (ex.timing(tag)) ex.mark_begin(&ev);
-  for (int epi = 0; epi < EPI_COUNT; ++epi) {
-    std::vector<TcJob<BF>*> sel;
-    for (auto& j : jobs)
-      if (j->epi == epi) sel.push_back(j.get());
-    for (size_t i = 0; i < sel.size(); i += GROUP_MAX) {
-      const int n = (int)std::min<size_t>(GROUP_MAX, sel.size() - i);
-      if (n == 1) tc_launch<BF, 1>(ex, epi, &sel[i], 1);
-      else tc_launch<BF, GROUP_MAX>(ex, epi, &sel[i], n);
+  for (int epi = 0; epi < EPI_COUNT; ++epi)
+    for (int tn : {TN, 128}) {
+      std::vector<TcJob<BF>*> sel;
+      for (auto& j : jobs)
+        if (j->epi == epi && j->tn == tn) sel.push_back(j.get());
+      for (size_t i = 0; i < sel.size(); i += GROUP_MAX) {
+        const int n = (int)std::min<size_t>(GROUP_MAX, sel.size() - i);
+        if (n == 1) tc_launch<BF, 1>(ex, epi, tn, &sel[i], 1);
+        else tc_launch<BF, GROUP_MAX>(ex, epi, tn, &sel[i], n);
+      }
     }
-  }
   for (auto& j : jobs) tc_finish<BF>(ex, *j);
   if (ev) ex.mark_end(tag, ev, flops);
 }
@@ -1709,7 +1725,7 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   job.mB = mB;
   job.a = a;
   TcJob<true>* one = &job;
-  tc_launch_group<true, EPI_PART, 1>(ex, &one, 1);
+  tc_launch_group<true, EPI_PART, 1, TN>(ex, &one, 1);
   const size_t rows = (size_t)g.batch * g.M;
   const int piece = rows * ((g.N + ROW_PIECE - 1) / ROW_PIECE) >= (size_t)ex.sm_count * 64 ? ROW_PIECE : 32;
   const size_t items = rows * ((g.N + piece - 1) / piece);
