@@ -420,16 +420,40 @@ __global__ void oz_digits_kernel(const double* __restrict__ src, CIdx rix, CIdx 
 // Both passes in one kernel for rows of at most a few thousand elements: one warp per staged
 // row finds the row's exponent (warp maximum, no atomics) and then writes its digits (the second
 // read of the row comes from L1/L2). Writes emax like the two-pass version.
-__global__ void oz_stage_rows_kernel(const double* __restrict__ src, CIdx rix, CIdx kix, CIdx bix, int rows, int K,
-                                     int batch, int rows_pad, int k_pad, int rev, unsigned* __restrict__ emax,
-                                     __nv_bfloat16* __restrict__ out) {
+// The two operands of a product staged by one launch: their descriptors, and the warps' rows
+// numbered across both (rows of A first).
+struct OzStageDesc {
+  const double* src;
+  CIdx rix, kix, bix;
+  int rows, batch, rows_pad, rev;
+  unsigned* emax;
+  __nv_bfloat16* out;
+};
+struct OzStagePair {
+  OzStageDesc d[2];
+  long long row0[3];
+  int K, k_pad;
+};
+
+__global__ void oz_stage_rows_kernel(const __grid_constant__ OzStagePair P) {
   const int lane = threadIdx.x & 31;
-  const long long items = (long long)batch * rows_pad;
+  const long long items = P.row0[2];
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int K = P.K, k_pad = P.k_pad;
   const size_t row_len = (size_t)OZ_S * k_pad;
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-  for (long long q = w0; q < items; q += nw) {
+  for (long long it = w0; it < items; it += nw) {
+    const int which = it >= P.row0[1] ? 1 : 0;
+    const OzStageDesc& D = P.d[which];
+    const double* src = D.src;
+    const CIdx& rix = D.rix;
+    const CIdx& kix = D.kix;
+    const CIdx& bix = D.bix;
+    const int rows = D.rows, rows_pad = D.rows_pad, rev = D.rev;
+    unsigned* emax = D.emax;
+    __nv_bfloat16* out = D.out;
+    const long long q = it - P.row0[which];  // staged row b * rows_pad + r of this operand
     const int b = (int)(q / rows_pad), r = (int)(q - (long long)b * rows_pad);
     __nv_bfloat16* row = out + (size_t)q * row_len;
     if (r >= rows) {
@@ -1635,14 +1659,22 @@ void run_oz(const Exec& ex, const GemmArgs& g, const char* tag) {
   auto* fB = reinterpret_cast<__nv_bfloat16*>(stB.p);
   auto* eA = reinterpret_cast<unsigned*>(exA.p);
   auto* eB = reinterpret_cast<unsigned*>(exB.p);
+  if (g.K <= 2048) {  // short rows: one warp per row, both passes and both operands in one kernel
+    OzStagePair P;
+    memset(&P, 0, sizeof(P));
+    P.d[0] = OzStageDesc{g.A, g.am, g.ak, g.ab, g.M, g.batch, rowsA, 0, eA, fA};
+    P.d[1] = OzStageDesc{g.B, g.bn, g.bk, g.bb, g.N, g.batch, rowsB, 1, eB, fB};
+    P.row0[0] = 0;
+    P.row0[1] = (long long)g.batch * rowsA;
+    P.row0[2] = P.row0[1] + (long long)g.batch * rowsB;
+    P.K = g.K;
+    P.k_pad = k_pad;
+    oz_stage_rows_kernel<<<blocks_for_rows((size_t)P.row0[2]), 256, 0, ex.stream>>>(P);
+    ex.count();
+  }
   auto stage = [&](const double* src, const CIdx& rix, const CIdx& kix, const CIdx& bix, int rows, int rows_pad,
                    int rev, unsigned* e, __nv_bfloat16* f) {
-    if (g.K <= 2048) {  // short rows: one warp per row, both passes in one kernel
-      oz_stage_rows_kernel<<<blocks_for_rows((size_t)g.batch * rows_pad), 256, 0, ex.stream>>>(
-          src, rix, kix, bix, rows, g.K, g.batch, rows_pad, k_pad, rev, e, f);
-      ex.count();
-      return;
-    }
+    if (g.K <= 2048) return;  // staged above
     CC_CUDA(cudaMemsetAsync(e, 0, (size_t)g.batch * rows_pad * sizeof(unsigned), ex.stream));
     const size_t pieces1 = (size_t)g.batch * rows * ((g.K + ROW_PIECE - 1) / ROW_PIECE);
     oz_rowexp_kernel<<<blocks_for_rows(pieces1), 256, 0, ex.stream>>>(src, rix, kix, bix, rows, g.K, g.batch,
