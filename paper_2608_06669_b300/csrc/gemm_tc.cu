@@ -104,16 +104,20 @@ constexpr int ROW_PIECE = 256;
 // operand, three segments [hi|hi|lo] and [hi|lo|hi] on the two operands give the three-pass
 // split product hi hi + hi lo + lo hi along one long k. One warp per piece of a staged row:
 // the row's source offset is located once, and the lanes walk k.
+// An operand whose rows are contiguous in the source and whose k is strided (tr = 1) is staged
+// by 32 x 32 tiles instead: a warp reads the tile down its rows, one k per step (coalesced),
+// and writes it along k through shared memory.
 // Several operands staged by one launch: their descriptors and the prefix sums of their work
-// items (batch x rows_pad x row pieces each) are a grid-constant parameter, and every warp walks
-// the combined item list, finding its operand by the prefix sums.
+// items (batch x rows_pad x row pieces each, or batch x row tiles x k tiles) are a grid-constant
+// parameter, and every warp walks the combined item list, finding its operand by the prefix sums.
 struct GatherDesc {
   const double* src;
   void* out;
   CIdx rix, kix, bix;
-  int rows, K, batch, rows_pad, k_pad, nseg, seg_lo;
+  int rows, K, batch, rows_pad, k_pad, nseg, seg_lo, tr;
 };
 constexpr int GATHER_MAX = 24;
+constexpr int GATHER_THREADS = 256;
 struct GatherList {
   GatherDesc d[GATHER_MAX];
   long long item0[GATHER_MAX + 1];
@@ -121,8 +125,10 @@ struct GatherList {
 };
 
 template <typename T>
-__global__ void gather_kernel(const __grid_constant__ GatherList L) {
+__global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const __grid_constant__ GatherList L) {
+  __shared__ float tiles[GATHER_THREADS / 32][32 * 33];
   const int lane = threadIdx.x & 31;
+  float* tile = tiles[threadIdx.x >> 5];
   const long long total = L.item0[L.n];
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -130,6 +136,38 @@ __global__ void gather_kernel(const __grid_constant__ GatherList L) {
   for (long long it = w0; it < total; it += nw) {
     while (it >= L.item0[gi + 1]) ++gi;  // a warp's items only grow
     const GatherDesc& d = L.d[gi];
+    if (d.tr) {
+      const int rtiles = (d.rows_pad + 31) >> 5, ktiles = (d.k_pad + 31) >> 5;
+      const long long li = it - L.item0[gi];
+      const long long q = li / ktiles;  // row tile b * rtiles + rt
+      const int k0 = (int)(li - q * ktiles) << 5;
+      const int b = (int)(q / rtiles), r0 = (int)(q - (long long)b * rtiles) << 5;
+      const bool rv = r0 + lane < d.rows;
+      const double* src = d.src + cidx(d.bix, b) + (rv ? cidx(d.rix, r0 + lane) : 0);
+      CWalk kw;
+      kw.init(d.kix, k0 + lane);
+      const long long koff = kw.off;  // lane j holds the offset of k0 + j
+      const int kn = min(32, d.K - k0);
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const long long o = __shfl_sync(0xffffffffu, koff, j);
+        tile[lane * 33 + j] = (rv && j < kn) ? (float)src[o] : 0.0f;
+      }
+      __syncwarp();
+      const int k = k0 + lane;
+      const int rn = min(32, d.rows_pad - r0);
+      const size_t row_len = (size_t)d.nseg * d.k_pad;
+      if (k < d.k_pad) {
+        for (int j = 0; j < rn; ++j) {
+          T hi, lo;
+          split(tile[j * 33 + lane], hi, lo);
+          T* row = static_cast<T*>(d.out) + ((size_t)b * d.rows_pad + r0 + j) * row_len;
+          for (int s = 0; s < d.nseg; ++s) row[(size_t)s * d.k_pad + k] = ((d.seg_lo >> s) & 1) ? lo : hi;
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     const int pieces = (d.k_pad + ROW_PIECE - 1) / ROW_PIECE;
     const size_t row_len = (size_t)d.nseg * d.k_pad;
     const long long li = it - L.item0[gi];
@@ -1336,11 +1374,13 @@ struct GatherBatch {
       for (int j = 0; j < L.n; ++j) {
         const GatherDesc& d = pend[i + j];
         L.d[j] = d;
-        L.item0[j + 1] = L.item0[j] + (long long)d.batch * d.rows_pad * ((d.k_pad + ROW_PIECE - 1) / ROW_PIECE);
+        const long long per_b = d.tr ? (long long)((d.rows_pad + 31) / 32) * ((d.k_pad + 31) / 32)
+                                     : (long long)d.rows_pad * ((d.k_pad + ROW_PIECE - 1) / ROW_PIECE);
+        L.item0[j + 1] = L.item0[j] + (long long)d.batch * per_b;
       }
       const long long items = L.item0[L.n];
       const int blocks = (int)std::max<long long>(1, std::min<long long>((items + 7) / 8, (long long)ex.sm_count * 16));
-      gather_kernel<T><<<blocks, 256, 0, ex.stream>>>(L);
+      gather_kernel<T><<<blocks, GATHER_THREADS, 0, ex.stream>>>(L);
       ex.count();
     }
     pend.clear();
@@ -1408,6 +1448,9 @@ void tc_prepare(const Exec& ex, cc_precision prec, const GemmArgs& g, TcJob<BF>&
     d.k_pad = k_pad;
     d.nseg = nseg;
     d.seg_lo = seg_lo;
+    // the stride of a compound index's innermost mode of extent > 1
+    auto inner = [](const CIdx& c) { return c.e2 > 1 ? c.s2 : c.e1 > 1 ? c.s1 : c.s0; };
+    d.tr = (g.K > 1 && inner(kix) != 1 && rows > 1 && inner(rix) == 1) ? 1 : 0;
     gb.pend.push_back(d);
     return reinterpret_cast<T*>(dst);
   };
